@@ -1,0 +1,442 @@
+#!/usr/bin/env python
+"""Benchmark of the CSR-k SpMV hot path on GB300.
+
+Workload (one "step"): y = A x on two 128^3 stencil matrices, 7-point (n = 2,097,152,
+nnz = 14,581,760) and 27-point (nnz = 55,742,968); FP64 values diagonally dominant with
+off-diagonals U[-1,0), int32 indices; the input rows/columns carry a random symmetric
+permutation (seed 3) that the CSR-k reorder (RCM) undoes; CSR-3 with super-rows of 32
+rows and super-super-rows of 8 super-rows; x ~ U[-1,1] (seed 2).  Each step runs, per
+matrix: permute x into the reordered numbering, the CSR-3 kernel, unpermute y -- the
+whole device path of a natural-numbering csrk_spmv call.  Inputs are resident in HBM
+and each step's working set (~930 MB) exceeds the 129 MB L2, so no flush is needed.
+
+Metric: GFLOP/s (2 flops per stored nonzero per SpMV), whole job over all ranks.
+Roofline: HBM bytes of the dominant kernel (the 27-point CSR-3 launch) per launch over its
+mean CUDA-event duration, against the measured copy bandwidth.
+
+--impl reference times the FP64 CPU oracle (single thread, plain CSR loop) on the host
+cores on a bounded sample of the same workload.
+
+Multi-GPU: replicas (one independent copy of the workload per rank, no collective on
+the data path); value = all ranks' flops / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+SIDE = 128
+SR, SSR = 32, 8
+MATRICES = (("stencil7", 7), ("stencil27", 27))
+
+# DRAM traffic per launch of the dominant kernel from an ncu capture (see
+# profiles/csr3_tma_27pt_128cubed_f64.md), valid only for the kernel source it was taken on.
+NCU_TRAFFIC = {}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha1()
+    for f in ("kernels.cuh", "launch_impl.cuh", "spmv_f64.cu"):
+        with open(os.path.join(ROOT, "paper_2203_05096_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def build_matrices(side=SIDE, only=None):
+    n = side ** 3
+    labels = synth.vectors.permutation(n, 3)
+    out = []
+    for name, pts in MATRICES:
+        if only and name != only:
+            continue
+        out.append((name, synth.stencil_3d(side, side, side, pts, "random_dd", 3, labels=labels)))
+    return out
+
+
+def alg_bytes_spmv(n, nnz, nsr, nssr, val_bytes=8, x_bytes=8):
+    # every stored value and column index, rowptr, sr_ptr, the 32-byte SSR descriptors,
+    # x read once and y written once (beta = 0)
+    return (val_bytes + 4) * nnz + 4 * (n + 1) + 4 * (nsr + 1) + 32 * nssr + x_bytes * n + x_bytes * n
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", str(self.idx)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in out.strip().splitlines():
+            p = [t.strip() for t in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def visible_gpu_index(local_rank):
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        ids = [v.strip() for v in vis.split(",") if v.strip()]
+        if local_rank < len(ids) and ids[local_rank].isdigit():
+            return int(ids[local_rank])
+    return local_rank
+
+
+def cpu_oracle_gflops(mats, seconds):
+    """The FP64 oracle (plain C row loop, one thread) on whole matrices, repeated until
+    `seconds` have passed."""
+    from oracle import spmv as ospmv
+    x = {}
+    flops = 0.0
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        for name, a in mats:
+            if name not in x:
+                x[name] = synth.uniform_vector(a.n, 2)
+            ospmv.csr_spmv(a.n, a.rowptr, a.colidx, a.vals, x[name])
+            flops += 2.0 * a.nnz
+        reps += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = time.perf_counter() - t0
+    return flops / dt / 1e9, f"{reps} full SpMV pass(es) over both 128^3 matrices in {dt:.1f} s"
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args, world, rank, local):
+    import ctypes
+
+    import torch
+    from paper_2203_05096_gb300 import csrk
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    lib = csrk.lib()
+    mats = build_matrices(args.side, args.only)
+    stream = torch.cuda.current_stream(dev)
+    sp = stream.cuda_stream
+    state = []
+    for name, a in mats:
+        h = csrk.create(a.n, a.rowptr, a.colidx, a.vals, args.dtype)
+        csrk.reorder(h, "rcm", want_perm=False)
+        csrk.set_sizes(h, SR, SSR)
+        if args.config:
+            csrk.set_config(h, **{k: int(v) for k, v in (kv.split("=") for kv in args.config.split(","))})
+        inf = csrk.info(h)
+        x = torch.tensor(synth.uniform_vector(a.n, 2), dtype=torch.float64, device=dev)
+        xp, yp, y = torch.empty_like(x), torch.empty_like(x), torch.empty_like(x)
+        state.append(dict(name=name, a=a, h=h, info=inf, x=x, xp=xp, yp=yp, y=y,
+                          cfg=csrk.tuned_config(h)))
+
+    perm_fn, spmv_fn = lib.csrk_permute, lib.csrk_spmv
+    VP = csrk.VEC_PERMUTED
+
+    def step(events=None, i=0):
+        for j, s in enumerate(state):
+            h = s["h"]
+            rc = perm_fn(h, 0, 1, s["x"].data_ptr(), 1, s["xp"].data_ptr(), 1, 0, sp)
+            if events is not None:
+                events[j][0][i].record(stream)
+            rc |= spmv_fn(h, 1.0, s["xp"].data_ptr(), 0.0, s["yp"].data_ptr(), VP, sp)
+            if events is not None:
+                events[j][1][i].record(stream)
+            rc |= perm_fn(h, 1, 1, s["yp"].data_ptr(), 1, s["y"].data_ptr(), 1, 0, sp)
+            if rc:
+                raise RuntimeError(lib.csrk_last_error().decode())
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    # correctness guard on sampled rows before timing
+    from oracle import spmv as ospmv
+    for s in state:
+        rows = np.random.default_rng(1).integers(0, s["a"].n, 2000)
+        ref = ospmv.csr_spmv_rows(s["a"].rowptr, s["a"].colidx, s["a"].vals, s["x"].cpu().numpy(), rows)
+        scale = ospmv.abs_row_scale(s["a"].rowptr, s["a"].colidx, s["a"].vals, s["x"].cpu().numpy(), rows=rows)
+        got = s["y"].cpu().numpy()[rows]
+        tol = 1e-12 if args.dtype == "f64" else 2.0 ** -8
+        if np.any(np.abs(got - ref) > tol * scale):
+            raise RuntimeError(f"{s['name']}: result check failed before timing")
+
+    K = args.steps
+    events = [[[torch.cuda.Event(enable_timing=True) for _ in range(K)] for _ in range(2)] for _ in state]
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(visible_gpu_index(local))
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    torch.cuda.synchronize()
+    t_start.record(stream)
+    wall0 = time.perf_counter()
+    for i in range(K):
+        step(events, i)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    clocks = sampler.stop()
+    if dist is not None:
+        dist.barrier()
+    ms = t_start.elapsed_time(t_end)
+    kern_ms = [[events[j][0][i].elapsed_time(events[j][1][i]) for i in range(K)] for j in range(len(state))]
+    if dist is not None:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    status = sum(csrk.device_status(s["h"]) for s in state)
+    if status:
+        raise RuntimeError("device status word set during the timed region")
+
+    flops_step = sum(2.0 * s["a"].nnz for s in state)
+    value = world * K * flops_step / (ms * 1e-3) / 1e9
+
+    # roofline of the dominant kernel: the 27-point CSR-3 launch
+    peak, peak_kind = measured_peaks()
+    vb = {"f64": 8, "f32": 4, "bf16": 2}[args.dtype]
+    dom = max(range(len(state)), key=lambda j: statistics.mean(kern_ms[j]))
+    sd = state[dom]
+    inf = sd["info"]
+    abytes = alg_bytes_spmv(inf["n"], inf["nnz"], inf["nsr"], inf["nssr"], vb)
+    kmean = statistics.mean(kern_ms[dom])
+    achieved = abytes / (kmean * 1e-3) / 1e9
+    khash = kernel_source_hash()
+    tr = NCU_TRAFFIC.get((sd["name"], args.dtype))
+    traffic = tr["bytes"] if tr and tr["kernel_hash"] == khash else None
+
+    per_matrix = {}
+    for j, s in enumerate(state):
+        inf = s["info"]
+        km = statistics.mean(kern_ms[j])
+        b = alg_bytes_spmv(inf["n"], inf["nnz"], inf["nsr"], inf["nssr"], vb)
+        per_matrix[s["name"]] = {"n": inf["n"], "nnz": inf["nnz"], "kernel_us": round(km * 1e3, 2),
+                                 "kernel_min_us": round(min(kern_ms[j]) * 1e3, 2),
+                                 "kernel_gflops": round(2.0 * inf["nnz"] / (km * 1e-3) / 1e9, 1),
+                                 "kernel_gbs": round(b / (km * 1e-3) / 1e9, 1),
+                                 "kernel_frac_of_peak": round(b / (km * 1e-3) / 1e9 / peak, 3),
+                                 "config": s["cfg"]}
+
+    # end to end: the public call with host vectors (pinned), copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        hx = [torch.tensor(synth.uniform_vector(s["a"].n, 2), dtype=torch.float64).pin_memory() for s in state]
+        hy = [torch.empty(s["a"].n, dtype=torch.float64).pin_memory() for s in state]
+        HV = csrk.HOST_VECTORS
+        E = max(5, min(args.steps // 10, 200))
+
+        def e2e_step():
+            for j, s in enumerate(state):
+                if spmv_fn(s["h"], 1.0, hx[j].data_ptr(), 0.0, hy[j].data_ptr(), HV, sp):
+                    raise RuntimeError(lib.csrk_last_error().decode())
+        for _ in range(3):
+            e2e_step()
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(E):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ems = e0.elapsed_time(e1)
+        if dist is not None:
+            t = torch.tensor([ems], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ems = float(t.item())
+        e2e = {"value": round(world * E * flops_step / (ems * 1e-3) / 1e9, 2), "unit": "GFLOP/s",
+               "h2d_bytes_per_step": int(sum(8 * s["a"].n for s in state)),
+               "d2h_bytes_per_step": int(sum(8 * s["a"].n for s in state))}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        g, sample = cpu_oracle_gflops(mats, args.cpu_seconds)
+        cpu = {"value": round(g, 3), "unit": "GFLOP/s", "cores": 1, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        line = {
+            "metric": "SpMV GFLOP/s (CSR-3, 128^3 7-point + 27-point stencils, FP64)",
+            "value": round(value, 2),
+            "unit": "GFLOP/s",
+            "n_gpus": world,
+            "steps": K,
+            "warmup": args.warmup,
+            "ms_per_step": round(ms / K, 5),
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": args.dtype,
+            "data": "synthetic",
+            "config": {"workload": "128^3 7-point and 27-point random diagonally dominant stencils, "
+                                   "random symmetric permutation undone by RCM, CSR-3 SR=32 rows, SSR=8 SRs, "
+                                   "y=Ax per matrix per step (permute x, CSR-3 kernel, unpermute y)",
+                       "sr": SR, "ssr": SSR, "l2": "inputs larger than L2 (~930 MB per step vs 129 MB)",
+                       "parallelism": f"replicas x{world}", "per_matrix": per_matrix},
+            "roofline": {"bound": "hbm", "kernel": f"csr3 {state[dom]['name']}",
+                         "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "traffic": traffic,
+                         "alg_bytes_per_launch": int(abytes), "peak_kind": peak_kind,
+                         "kernel_hash": khash},
+            "e2e": e2e,
+            "gpu_launches": K * 3 * len(state),
+            "clocks": clocks,
+            "cpu_baseline": cpu,
+            "wall_s_timed": round(wall, 3),
+        }
+        print(json.dumps(line), flush=True)
+    for s in state:
+        csrk.destroy(s["h"])
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args, world, rank, local):
+    """The FP64 CPU oracle as it stands, on the host cores, each step a bounded block of
+    rows of both matrices (rotating through the matrix)."""
+    if rank != 0:
+        return
+    from oracle import spmv as ospmv
+    mats = build_matrices(args.side, args.only)
+    xs = [synth.uniform_vector(a.n, 2) for _, a in mats]
+    budget = max(0.005, min(0.5, 60.0 / max(1, args.steps + args.warmup)))
+    # calibrate rows per block on the densest matrix
+    a27 = mats[-1][1]
+    probe = np.arange(0, 20000, dtype=np.int64)
+    t0 = time.perf_counter()
+    ospmv.csr_spmv_rows(a27.rowptr, a27.colidx, a27.vals, xs[1], probe)
+    per_row = (time.perf_counter() - t0) / probe.size
+    rows_per_block = max(1000, int(budget / 2 / max(per_row, 1e-9)))
+    cursor = [0, 0]
+
+    def step():
+        fl = 0.0
+        for j, (_, a) in enumerate(mats):
+            b = cursor[j]
+            e = min(a.n, b + rows_per_block)
+            rows = np.arange(b, e, dtype=np.int64)
+            ospmv.csr_spmv_rows(a.rowptr, a.colidx, a.vals, xs[j], rows)
+            fl += 2.0 * float(a.rowptr[e] - a.rowptr[b])
+            cursor[j] = 0 if e >= a.n else e
+        return fl
+
+    for _ in range(args.warmup):
+        step()
+    flops = 0.0
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        flops += step()
+    dt = time.perf_counter() - t0
+    value = flops / dt / 1e9
+    sample = f"{rows_per_block} rows of each matrix per step, {args.steps} steps, {dt:.1f} s"
+    line = {
+        "impl": "reference",
+        "metric": "SpMV GFLOP/s (CSR-3, 128^3 7-point + 27-point stencils, FP64)",
+        "value": round(value, 3), "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "128^3 7-point and 27-point random diagonally dominant stencils, "
+                               "random symmetric permutation undone by RCM, CSR-3 SR=32 rows, SSR=8 SRs, "
+                               "y=Ax per matrix per step (permute x, CSR-3 kernel, unpermute y)"},
+        "cpu_baseline": {"value": round(value, 3), "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(value, 3), "unit": "GFLOP/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=2000)
+    p.add_argument("--warmup", type=int, default=20)
+    p.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    p.add_argument("--dtype", choices=("f64", "f32", "bf16"), default="f64")
+    p.add_argument("--config", default="", help="force a launch config, e.g. kernel=0,lanes=1,warps=8")
+    p.add_argument("--cpu-seconds", type=float, default=10.0)
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--side", type=int, default=SIDE, help="grid side (profiling runs use a smaller case)")
+    p.add_argument("--only", choices=[m for m, _ in MATRICES], default=None)
+    args = p.parse_args()
+    if args.warmup < 3:
+        p.error("--warmup must be >= 3")
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, world, rank, local)
+    else:
+        run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

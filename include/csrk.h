@@ -1,0 +1,217 @@
+/*
+ * csrk.h -- C ABI of the GB300 CSR-k sparse matrix-vector library.
+ *
+ * The library computes y = alpha*A*x + beta*y (and the k-right-hand-side form
+ * Y = alpha*A*X + beta*Y) for a square sparse matrix A held in CSR-k form: plain CSR
+ * (row_ptr, col_idx, vals), its rows renumbered by a bandwidth-reducing permutation, and
+ * the rows grouped into super-rows and super-super-rows described by two extra pointer
+ * arrays (Lane & Booth, arXiv 2203.05096: problem statement Sec. 1; CSR Sec. 2.1;
+ * CSR-k / CSR-3 and its pointer arrays Sec. 2.2 and Fig. 1; the GPU mapping of
+ * super-super-rows to thread blocks and super-rows to the next thread level Sec. 3).
+ *
+ * Conventions shared by every entry point
+ *   - Every function returns a csrk_status.  CSRK_OK is 0.  csrk_last_error() returns a
+ *     message for the calling thread's last failure (static storage, valid until that
+ *     thread's next call).  No C++ exception crosses this boundary.
+ *   - Host arrays passed in are copied; the caller keeps ownership and may free them as
+ *     soon as the call returns.
+ *   - Vector arguments of the compute calls are DEVICE pointers owned by the caller
+ *     (e.g. PyTorch tensors), aligned to their element size, unless CSRK_HOST_VECTORS is
+ *     given.  x and y (X and Y) must not overlap.
+ *   - Device work is enqueued on the given CUDA stream (a cudaStream_t passed as void*;
+ *     NULL is the legacy default stream) without synchronising the host, except where a
+ *     function says otherwise.  Errors found on the host are reported synchronously.
+ *     Device-side failures (a bounded wait that ran out) set a status word on the device;
+ *     csrk_device_status() reads it.
+ *   - The library owns all device copies of A and its own scratch vectors.  It allocates
+ *     them on first use (the first compute call after csrk_set_sizes / csrk_set_pointers,
+ *     or the first call that needs a larger scratch size) on the device current at that
+ *     time; later calls must be made with the same device current.
+ *   - Life cycle: csrk_create -> [csrk_reorder] -> csrk_set_sizes or csrk_set_pointers
+ *     -> compute calls ...; csrk_set_sizes may be called again (the pointer arrays and
+ *     device copies are rebuilt); csrk_reorder after the pointers exist returns
+ *     CSRK_ERR_STATE.  A handle is not thread-safe: one thread uses it at a time.
+ */
+#ifndef CSRK_H
+#define CSRK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct csrk_matrix* csrk_handle;
+typedef struct csrk_batch* csrk_batch_handle;
+
+/* Storage precision of A's values on the device.  Narrowing from the FP64 input rounds
+ * to nearest, ties to even, once and directly from FP64 (BF16 never through FP32). */
+typedef enum { CSRK_F64 = 0, CSRK_F32 = 1, CSRK_BF16 = 2 } csrk_dtype;
+
+typedef enum {
+    CSRK_OK = 0,
+    CSRK_ERR_ARG = 1,          /* bad argument: NULL where not allowed, size out of range */
+    CSRK_ERR_MATRIX = 2,       /* invalid CSR: rowptr not monotone or not starting at 0,
+                                  column out of [0, n), repeated column in a row,
+                                  nnz >= 2^31 */
+    CSRK_ERR_STATE = 3,        /* call out of order for this handle's life cycle */
+    CSRK_ERR_ALLOC = 4,        /* host or device allocation failed */
+    CSRK_ERR_CUDA = 5,         /* a CUDA runtime call failed (message has the CUDA error) */
+    CSRK_ERR_UNSUPPORTED = 6,  /* valid request this build does not implement */
+    CSRK_ERR_TIMEOUT = 7,      /* a device-side bounded wait ran out (see csrk_device_status) */
+    CSRK_ERR_NOT_CONVERGED = 8 /* an iterative solve stopped at maxit above its tolerance */
+} csrk_status;
+
+/* Flags of the compute calls (bitwise OR). */
+#define CSRK_VEC_PERMUTED 1u  /* x/y already in the reordered numbering: skip the device
+                                 permute of x and unpermute of y */
+#define CSRK_ACC_F32      2u  /* accumulate row sums in FP32 (default FP64) */
+#define CSRK_X_F32        4u  /* x and y are FP32 (default FP64) */
+#define CSRK_HOST_VECTORS 8u  /* x and y are HOST pointers: the call copies x in and y out
+                                 through its own device scratch and returns after the
+                                 copy of y has completed (synchronous) */
+
+/* Reordering methods for csrk_reorder. */
+#define CSRK_REORDER_NONE 0   /* keep the input numbering (perm = identity) */
+#define CSRK_REORDER_RCM  1   /* reverse Cuthill-McKee of the symmetrised pattern */
+
+/* ---------------------------------------------------------------------------------
+ * csrk_create: take a square n x n CSR matrix (Sec. 2.1).
+ *   n       rows = columns, 0 <= n < 2^31
+ *   rowptr  host, n+1 entries, rowptr[0] == 0, non-decreasing; nnz = rowptr[n] < 2^31
+ *   colidx  host, nnz column indices in [0, n); a row's columns may come in any order
+ *           (they are sorted, carrying their values) but may not repeat
+ *   vals    host, nnz FP64 values (NaN / Inf are stored as given)
+ *   dtype   storage precision used by csrk_spmv / csrk_spmm
+ *   out     receives the handle (NULL on failure)
+ * Errors: CSRK_ERR_ARG, CSRK_ERR_MATRIX (with the first offending row in the message),
+ * CSRK_ERR_ALLOC.  Host only; touches no GPU.
+ * --------------------------------------------------------------------------------- */
+int csrk_create(int32_t n, const int32_t* rowptr, const int32_t* colidx, const double* vals,
+                csrk_dtype dtype, csrk_handle* out);
+
+/* csrk_reorder: renumber rows and columns by a bandwidth-reducing permutation so that a
+ * super-row's rows share x entries (Sec. 2.1 RCM; the paper's own Band-k ordering,
+ * Listing 2, is not implemented).  B = P A P^T with B[i][j] = A[perm[i]][perm[j]], each
+ * row's columns ascending.
+ *   method    CSRK_REORDER_NONE or CSRK_REORDER_RCM
+ *   perm_out  optional host array of n entries receiving perm (perm[new] = old)
+ * RCM reading: graph of A + A^T without self-loops; each component starts at the
+ * unvisited vertex of least degree (smallest index on ties), moved by the George-Liu
+ * pseudo-peripheral search (least-degree vertex of the last BFS level, smallest index on
+ * ties, while the level structure deepens, at most 8 moves); Cuthill-McKee order with
+ * children by (degree, index); the whole sequence reversed.
+ * Errors: CSRK_ERR_STATE after the pointers exist, CSRK_ERR_ARG, CSRK_ERR_ALLOC.
+ * Host only. */
+int csrk_reorder(csrk_handle h, int method, int32_t* perm_out);
+
+/* csrk_set_sizes: build sr_ptr / ssr_ptr for fixed sizes (Sec. 2.2): every super-row
+ * holds sr rows and every super-super-row ssr super-rows, the last of each possibly
+ * fewer.  sr = ssr = 0 asks the autotuner to choose (it times candidates on the GPU,
+ * so that form needs a device; the choice is cached per matrix shape, see
+ * csrk_tuned_config).  Any other non-positive size is CSRK_ERR_ARG.
+ * Host only for explicit sizes. */
+int csrk_set_sizes(csrk_handle h, int32_t sr, int32_t ssr);
+
+/* csrk_set_pointers: give the super-row and super-super-row pointer arrays explicitly
+ * (variable sizes, e.g. Fig. 1: sr_ptr = {0,2,5,7,9}, ssr_ptr = {0,2,4}).
+ *   nsr     number of super-rows; sr_ptr has nsr+1 entries, sr_ptr[0] = 0,
+ *           sr_ptr[nsr] = n, non-decreasing
+ *   nssr    number of super-super-rows; ssr_ptr has nssr+1 entries, ssr_ptr[0] = 0,
+ *           ssr_ptr[nssr] = nsr, non-decreasing
+ * Errors: CSRK_ERR_ARG for arrays that break these rules.  Host only. */
+int csrk_set_pointers(csrk_handle h, int32_t nsr, const int32_t* sr_ptr, int32_t nssr,
+                      const int32_t* ssr_ptr);
+
+/* csrk_spmv: y = alpha*A*x + beta*y with A's stored dtype.
+ *   x, y    n entries, FP64 (FP32 with CSRK_X_F32), in the input numbering unless
+ *           CSRK_VEC_PERMUTED; device pointers unless CSRK_HOST_VECTORS
+ *   beta    0 means y is write-only (its old contents, even NaN, are not read)
+ *   flags   CSRK_VEC_PERMUTED | CSRK_ACC_F32 | CSRK_X_F32 | CSRK_HOST_VECTORS
+ *   stream  cudaStream_t (NULL = default stream)
+ * FP64 values with CSRK_X_F32 are CSRK_ERR_UNSUPPORTED.  Without CSRK_VEC_PERMUTED the
+ * call permutes x into library scratch, runs the CSR-k kernel there and scatters the
+ * result back (y[perm[i]] = result[i]).  Errors: CSRK_ERR_STATE before the pointers
+ * exist, CSRK_ERR_ARG, CSRK_ERR_ALLOC, CSRK_ERR_CUDA. */
+int csrk_spmv(csrk_handle h, double alpha, const void* x, double beta, void* y,
+              unsigned flags, void* stream);
+
+/* csrk_spmm: Y = alpha*A*X + beta*Y for k right-hand sides, 1 <= k <= 64.
+ *   X       n x k, row-major, leading dimension ldx >= k (entry (i,c) at X[i*ldx + c])
+ *   Y       n x k, row-major, leading dimension ldy >= k
+ * Same flags, dtypes, numbering and errors as csrk_spmv; column c of Y is exactly what
+ * csrk_spmv would give for column c of X, up to the order of floating-point additions. */
+int csrk_spmm(csrk_handle h, int32_t k, double alpha, const void* X, int64_t ldx,
+              double beta, void* Y, int64_t ldy, unsigned flags, void* stream);
+
+/* csrk_permute: move a dense n x k block between the input numbering and the reordered
+ * numbering on the device (the permute / unpermute steps that csrk_spmv performs around
+ * its kernel when CSRK_VEC_PERMUTED is absent).
+ *   direction 0: out[i][c] = in[perm[i]][c]  (input numbering -> reordered)
+ *   direction 1: out[perm[i]][c] = in[i][c]  (reordered -> input numbering)
+ *   in, out    device pointers, row-major, leading dimensions ldi, ldo >= k; FP64, or FP32
+ *              with CSRK_X_F32 in flags; they must not overlap
+ * With no reordering (perm = identity) this is a plain strided copy.  Errors:
+ * CSRK_ERR_STATE before the pointers exist, CSRK_ERR_ARG, CSRK_ERR_CUDA. */
+int csrk_permute(csrk_handle h, int direction, int32_t k, const void* in, int64_t ldi,
+                 void* out, int64_t ldo, unsigned flags, void* stream);
+
+/* csrk_destroy: free the handle and every host and device buffer it owns, after
+ * synchronising the device.  NULL is a no-op. */
+int csrk_destroy(csrk_handle h);
+
+/* ---------------------------------------------------------------- inspection */
+
+/* csrk_info: sizes of the current form; any output pointer may be NULL.
+ *   n, nnz; nsr / nssr (0 before the pointers exist); sr / ssr the fixed sizes
+ *   (0 after csrk_set_pointers); dtype. */
+int csrk_info(csrk_handle h, int32_t* n, int64_t* nnz, int32_t* nsr, int32_t* nssr,
+              int32_t* sr, int32_t* ssr, int32_t* dtype);
+
+/* csrk_export: copy the host form out (any pointer may be NULL; arrays sized from
+ * csrk_info): perm (n), the reordered CSR rowptr (n+1) / colidx (nnz) / vals (nnz, FP64),
+ * sr_ptr (nsr+1), ssr_ptr (nssr+1).  The reordered arrays are plain CSR (Sec. 2.2: a
+ * CSR-k matrix stays readable by CSR consumers). */
+int csrk_export(csrk_handle h, int32_t* perm, int32_t* rowptr, int32_t* colidx,
+                double* vals, int32_t* sr_ptr, int32_t* ssr_ptr);
+
+/* csrk_export_values: the stored device-dtype values, in the reordered order, as the
+ * host converts them: dtype CSRK_F64 -> double[nnz], CSRK_F32 -> float[nnz],
+ * CSRK_BF16 -> uint16_t[nnz] bit patterns.  Host only. */
+int csrk_export_values(csrk_handle h, csrk_dtype dtype, void* out);
+
+/* csrk_model_sizes: the paper's constant-time size model (Sec. 4.1) for row density
+ * rdensity = nnz / n: arch 0 = Volta, 1 = Ampere coefficients; outputs the
+ * super-super-row size *ssrs and super-row size *srs after the rdensity case rules.
+ * The library uses it only to seed its autotuner. */
+int csrk_model_sizes(double rdensity, int arch, int32_t* ssrs, int32_t* srs);
+
+/* csrk_tuned_config: the launch configuration the handle will use:
+ *   kernel   0 = TMA-staged super-super-row kernel, 1 = direct-load kernel
+ *   lanes    lanes cooperating on one row (SpMV)
+ *   warps    consumer warps per thread block
+ *   stages   shared-memory pipeline depth (TMA kernel)
+ *   ctas     thread blocks per SM */
+int csrk_tuned_config(csrk_handle h, int32_t* kernel, int32_t* lanes, int32_t* warps,
+                      int32_t* stages, int32_t* ctas);
+
+/* csrk_set_config: force a launch configuration (same fields as csrk_tuned_config;
+ * a negative field keeps the current value).  Used by the autotuner and tests. */
+int csrk_set_config(csrk_handle h, int32_t kernel, int32_t lanes, int32_t warps,
+                    int32_t stages, int32_t ctas);
+
+/* csrk_device_status: synchronise the handle's work on `stream` and return the device
+ * status word (0 = clean; bit 0 = a pipeline wait ran out) in *status, then clear it.
+ * Returns CSRK_ERR_TIMEOUT when the word was non-zero. */
+int csrk_device_status(csrk_handle h, void* stream, int32_t* status);
+
+const char* csrk_last_error(void);
+
+/* Library build description (static string): compiled architectures and options. */
+const char* csrk_build_info(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CSRK_H */

@@ -1,0 +1,633 @@
+// C ABI entry points and the device runtime behind them: handle life cycle, one-time
+// upload of the CSR-k form, library-owned scratch vectors, launch configuration and the
+// permute -> CSR-3 kernel -> unpermute sequence of a compute call.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "csrk_internal.h"
+
+using namespace csrk;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg) {
+    g_last_error = msg;
+    return code;
+}
+int cuda_fail(cudaError_t e, const char* what) {
+    return fail(CSRK_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK_CUDA(call, what)                         \
+    do {                                            \
+        cudaError_t e_ = (call);                    \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+size_t val_size(int vt) { return vt == VAL_F64 ? 8 : (vt == VAL_F32 ? 4 : 2); }
+
+}  // namespace
+
+// ------------------------------------------------------------------ handle
+struct csrk_matrix {
+    CsrHost m;                     // current form (reordered after csrk_reorder)
+    std::vector<int32_t> perm;     // perm[new] = old; empty = identity
+    csrk_dtype dtype = CSRK_F64;
+    bool have_ptrs = false;
+    int32_t sr = 0, ssr = 0;       // fixed sizes (0 when given explicitly)
+    std::vector<int32_t> sr_ptr, ssr_ptr;
+    std::vector<SsrDesc> desc;
+    TileStats stats;
+    KernelConfig cfg;
+    bool cfg_set = false;
+    unsigned long long timeout_ns = 2000000000ull;
+
+    // device form
+    int device = -1;
+    int num_sms = 0;
+    int smem_per_sm = 0, smem_optin = 0;
+    bool dev_struct = false;       // rowptr/colidx/pointers/desc/perm uploaded
+    int32_t* d_rowptr = nullptr;
+    int32_t* d_colidx = nullptr;
+    void* d_vals[3] = {nullptr, nullptr, nullptr};
+    int32_t* d_sr_ptr = nullptr;
+    SsrDesc* d_desc = nullptr;
+    int32_t* d_perm = nullptr;
+    int32_t* d_status = nullptr;
+    // scratch: permuted x / y, and device copies of host vectors
+    void* d_scratch[4] = {nullptr, nullptr, nullptr, nullptr};
+    size_t scratch_bytes[4] = {0, 0, 0, 0};
+};
+
+namespace {
+
+void free_struct(csrk_matrix* h) {
+    cudaFree(h->d_rowptr);
+    cudaFree(h->d_colidx);
+    cudaFree(h->d_sr_ptr);
+    cudaFree(h->d_desc);
+    cudaFree(h->d_perm);
+    h->d_rowptr = h->d_colidx = h->d_sr_ptr = h->d_perm = nullptr;
+    h->d_desc = nullptr;
+    h->dev_struct = false;
+}
+
+void free_device(csrk_matrix* h) {
+    if (h->device < 0) return;
+    free_struct(h);
+    for (auto& v : h->d_vals) {
+        cudaFree(v);
+        v = nullptr;
+    }
+    for (int i = 0; i < 4; ++i) {
+        cudaFree(h->d_scratch[i]);
+        h->d_scratch[i] = nullptr;
+        h->scratch_bytes[i] = 0;
+    }
+    cudaFree(h->d_status);
+    h->d_status = nullptr;
+}
+
+// Allocate `count` elements of `esz` bytes plus 16 elements of zeroed padding (the TMA
+// kernel rounds slices out to 16-byte boundaries) and copy `count` elements from host.
+template <typename T>
+int upload_padded(T** dst, const void* src, size_t count, size_t esz, const char* what) {
+    const size_t bytes = (count + 16) * esz;
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) return fail(CSRK_ERR_ALLOC, std::string("cudaMalloc ") + what + ": " + cudaGetErrorString(e));
+    e = cudaMemset(p, 0, bytes);
+    if (e == cudaSuccess && count) e = cudaMemcpy(p, src, count * esz, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(p);
+        return cuda_fail(e, what);
+    }
+    *dst = static_cast<T*>(p);
+    return CSRK_OK;
+}
+
+int ensure_context(csrk_matrix* h) {
+    int dev = 0;
+    CK_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+    if (h->device >= 0 && h->device != dev)
+        return fail(CSRK_ERR_STATE, "handle's device copies live on device " + std::to_string(h->device) +
+                                        " but device " + std::to_string(dev) + " is current");
+    if (h->device < 0) {
+        h->device = dev;
+        CK_CUDA(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev), "attr");
+        CK_CUDA(cudaDeviceGetAttribute(&h->smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev), "attr");
+        CK_CUDA(cudaDeviceGetAttribute(&h->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev), "attr");
+        void* p = nullptr;
+        CK_CUDA(cudaMalloc(&p, 16), "cudaMalloc status");
+        CK_CUDA(cudaMemset(p, 0, 16), "cudaMemset status");
+        h->d_status = static_cast<int32_t*>(p);
+    }
+    return CSRK_OK;
+}
+
+int ensure_struct(csrk_matrix* h) {
+    if (h->dev_struct) return CSRK_OK;
+    const CsrHost& m = h->m;
+    int rc;
+    if ((rc = upload_padded(&h->d_rowptr, m.rowptr.data(), m.rowptr.size(), 4, "rowptr"))) return rc;
+    if ((rc = upload_padded(&h->d_colidx, m.colidx.data(), m.colidx.size(), 4, "colidx"))) return rc;
+    if ((rc = upload_padded(&h->d_sr_ptr, h->sr_ptr.data(), h->sr_ptr.size(), 4, "sr_ptr"))) return rc;
+    if ((rc = upload_padded(&h->d_desc, h->desc.data(), h->desc.size(), sizeof(SsrDesc), "desc"))) return rc;
+    if (!h->perm.empty())
+        if ((rc = upload_padded(&h->d_perm, h->perm.data(), h->perm.size(), 4, "perm"))) return rc;
+    h->dev_struct = true;
+    return CSRK_OK;
+}
+
+int ensure_vals(csrk_matrix* h, int vt) {
+    if (h->d_vals[vt]) return CSRK_OK;
+    const CsrHost& m = h->m;
+    const size_t nnz = m.vals.size();
+    if (vt == VAL_F64) return upload_padded(reinterpret_cast<double**>(&h->d_vals[vt]), m.vals.data(), nnz, 8, "vals");
+    if (vt == VAL_F32) {
+        std::vector<float> tmp(nnz);
+        narrow_f32(m.vals.data(), tmp.data(), (int64_t)nnz);
+        return upload_padded(reinterpret_cast<float**>(&h->d_vals[vt]), tmp.data(), nnz, 4, "vals f32");
+    }
+    std::vector<uint16_t> tmp(nnz);
+    narrow_bf16(m.vals.data(), tmp.data(), (int64_t)nnz);
+    return upload_padded(reinterpret_cast<uint16_t**>(&h->d_vals[vt]), tmp.data(), nnz, 2, "vals bf16");
+}
+
+int ensure_scratch(csrk_matrix* h, int slot, size_t bytes) {
+    if (h->scratch_bytes[slot] >= bytes) return CSRK_OK;
+    cudaFree(h->d_scratch[slot]);
+    h->d_scratch[slot] = nullptr;
+    h->scratch_bytes[slot] = 0;
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) return fail(CSRK_ERR_ALLOC, std::string("cudaMalloc scratch: ") + cudaGetErrorString(e));
+    h->d_scratch[slot] = p;
+    h->scratch_bytes[slot] = bytes;
+    return CSRK_OK;
+}
+
+int default_lanes(const csrk_matrix* h) {
+    const double mean = h->m.n ? (double)h->m.nnz() / h->m.n : 0.0;
+    if (mean <= 32) return 1;
+    if (mean <= 64) return 2;
+    if (mean <= 128) return 4;
+    if (mean <= 256) return 8;
+    return 32;
+}
+
+int smem_budget(const csrk_matrix* h, int ctas) {
+    int per_cta = h->smem_per_sm / std::max(1, ctas) - 1024;
+    return std::min(per_cta, h->smem_optin);
+}
+
+}  // namespace
+
+bool csrk::plan_stages(const TileStats& st, int val_bytes, int max_smem, int want_stages,
+                       StagePlan& plan) {
+    auto r16 = [](int64_t v) { return (v + 15) & ~int64_t(15); };
+    const int64_t srp = r16((int64_t)(st.max_srs + 8) * 4);
+    const int64_t rp = r16((int64_t)(st.max_rows + 8) * 4);
+    const int64_t col = r16((st.max_nnz + 8) * 4);
+    const int64_t val = r16((st.max_nnz + 16) * val_bytes);
+    int64_t stage = srp + rp + col + val;
+    stage = (stage + 127) & ~int64_t(127);
+    const int64_t header = 768;   // 16 stages x (2 mbarriers + one 32-byte descriptor)
+    int64_t fit = (max_smem - header) / stage;
+    int64_t s = std::min<int64_t>(fit, 16);
+    if (want_stages > 0) s = std::min<int64_t>(s, want_stages);
+    if (s < 2 || stage > (int64_t)UINT32_MAX) return false;
+    plan.off_srp = 0;
+    plan.off_rp = (uint32_t)srp;
+    plan.off_col = (uint32_t)(srp + rp);
+    plan.off_val = (uint32_t)(srp + rp + col);
+    plan.stage_bytes = (uint32_t)stage;
+    plan.header_bytes = (uint32_t)header;
+    plan.stages = (int)s;
+    return true;
+}
+
+int csrk::launch_csr3(const LaunchArgs& a, const KernelConfig& cfg, const StagePlan& plan,
+                      void* stream) {
+    switch (a.val_type) {
+        case VAL_F64: return launch_csr3_f64(a, cfg, plan, stream);
+        case VAL_F32: return launch_csr3_f32(a, cfg, plan, stream);
+        default: return launch_csr3_bf16(a, cfg, plan, stream);
+    }
+}
+
+namespace {
+
+// Resolve the launch configuration and stage plan for this handle and value type.
+int resolve_config(csrk_matrix* h, int vt, KernelConfig& cfg, StagePlan& plan) {
+    cfg = h->cfg;
+    if (!h->cfg_set) {
+        cfg = KernelConfig{};
+        cfg.lanes = default_lanes(h);
+    }
+    plan = StagePlan{};
+    if (cfg.kernel == 0) {
+        if (!plan_stages(h->stats, (int)val_size(vt), smem_budget(h, cfg.ctas), cfg.stages, plan)) {
+            if (h->cfg_set && h->cfg.kernel == 0)
+                return fail(CSRK_ERR_UNSUPPORTED, "super-super-rows too large for two shared-memory stages; "
+                                                  "choose smaller sizes or the direct kernel");
+            cfg.kernel = 1;   // the SSRs do not fit: fall back to direct loads
+        }
+    }
+    if (cfg.kernel == 1 && cfg.lanes != 1 && cfg.lanes != 4 && cfg.lanes != 32)
+        cfg.lanes = cfg.lanes < 4 ? 1 : (cfg.lanes < 32 ? 4 : 32);
+    return CSRK_OK;
+}
+
+int compute(csrk_matrix* h, int32_t k, bool spmm, double alpha, const void* X, int64_t ldx,
+            double beta, void* Y, int64_t ldy, unsigned flags, void* stream) {
+    if (!h) return fail(CSRK_ERR_ARG, "handle is NULL");
+    if (!h->have_ptrs) return fail(CSRK_ERR_STATE, "call csrk_set_sizes or csrk_set_pointers first");
+    const int32_t n = h->m.n;
+    if (n > 0 && (!X || !Y)) return fail(CSRK_ERR_ARG, "x / y is NULL");
+    if (X == Y && n > 0) return fail(CSRK_ERR_ARG, "x and y must not overlap");
+    if (k < 1 || k > 64) return fail(CSRK_ERR_ARG, "k must be in [1, 64]");
+    if (ldx < k || ldy < k) return fail(CSRK_ERR_ARG, "leading dimension smaller than k");
+    const bool x_f32 = flags & CSRK_X_F32;
+    const bool acc_f32 = flags & CSRK_ACC_F32;
+    const int vt = (int)h->dtype;
+    if (vt == VAL_F64 && (x_f32 || acc_f32))
+        return fail(CSRK_ERR_UNSUPPORTED, "FP64 values take FP64 vectors and FP64 accumulation");
+    if (acc_f32 && !x_f32)
+        return fail(CSRK_ERR_UNSUPPORTED, "FP32 accumulation needs FP32 vectors (CSRK_X_F32)");
+    int rc;
+    if ((rc = ensure_context(h))) return rc;
+    if ((rc = ensure_struct(h))) return rc;
+    if ((rc = ensure_vals(h, vt))) return rc;
+    if (n == 0) return CSRK_OK;
+
+    const size_t esz = x_f32 ? 4 : 8;
+    const bool host_vec = flags & CSRK_HOST_VECTORS;
+    const bool permuted = (flags & CSRK_VEC_PERMUTED) || h->perm.empty();
+    cudaStream_t s = (cudaStream_t)stream;
+    const void* xin = X;
+    void* yout = Y;
+    int64_t ldxin = ldx, ldyout = ldy;
+    if (host_vec) {
+        const size_t xb = (size_t)n * ldx * esz, yb = (size_t)n * ldy * esz;
+        if ((rc = ensure_scratch(h, 2, xb))) return rc;
+        if ((rc = ensure_scratch(h, 3, yb))) return rc;
+        CK_CUDA(cudaMemcpyAsync(h->d_scratch[2], X, xb, cudaMemcpyHostToDevice, s), "copy x to device");
+        if (beta != 0.0)
+            CK_CUDA(cudaMemcpyAsync(h->d_scratch[3], Y, yb, cudaMemcpyHostToDevice, s), "copy y to device");
+        xin = h->d_scratch[2];
+        yout = h->d_scratch[3];
+    }
+    const void* xk = xin;
+    void* yk = yout;
+    int64_t ldxk = ldxin, ldyk = ldyout;
+    if (!permuted) {
+        const size_t b = (size_t)n * k * esz;
+        if ((rc = ensure_scratch(h, 0, b))) return rc;
+        if ((rc = ensure_scratch(h, 1, b))) return rc;
+        int e = launch_gather_rows(xin, ldxin, h->d_scratch[0], k, h->d_perm, n, k, (int)esz, s);
+        if (e) return cuda_fail((cudaError_t)e, "permute x");
+        if (beta != 0.0) {
+            e = launch_gather_rows(yout, ldyout, h->d_scratch[1], k, h->d_perm, n, k, (int)esz, s);
+            if (e) return cuda_fail((cudaError_t)e, "permute y");
+        }
+        xk = h->d_scratch[0];
+        yk = h->d_scratch[1];
+        ldxk = ldyk = k;
+    }
+    KernelConfig cfg;
+    StagePlan plan;
+    if ((rc = resolve_config(h, vt, cfg, plan))) return rc;
+    LaunchArgs a{};
+    a.desc = h->d_desc;
+    a.sr_ptr = h->d_sr_ptr;
+    a.rowptr = h->d_rowptr;
+    a.colidx = h->d_colidx;
+    a.vals = h->d_vals[vt];
+    a.x = xk;
+    a.y = yk;
+    a.ldx = ldxk;
+    a.ldy = ldyk;
+    a.k = k;
+    a.nssr = (int32_t)h->desc.size();
+    a.alpha = alpha;
+    a.beta = beta;
+    a.status = h->d_status;
+    a.stats = h->stats;
+    a.val_type = vt;
+    a.x_f32 = x_f32;
+    a.acc_f32 = acc_f32;
+    a.spmm = spmm;
+    a.num_sms = h->num_sms;
+    a.timeout_ns = h->timeout_ns;
+    int e = launch_csr3(a, cfg, plan, s);
+    if (e == -1) return fail(CSRK_ERR_UNSUPPORTED, "kernel variant not compiled for this configuration");
+    if (e) return cuda_fail((cudaError_t)e, "CSR-3 kernel launch");
+    if (!permuted) {
+        e = launch_scatter_rows(h->d_scratch[1], k, yout, ldyout, h->d_perm, n, k, (int)esz, s);
+        if (e) return cuda_fail((cudaError_t)e, "unpermute y");
+    }
+    if (host_vec) {
+        CK_CUDA(cudaMemcpyAsync(Y, h->d_scratch[3], (size_t)n * ldy * esz, cudaMemcpyDeviceToHost, s),
+                "copy y to host");
+        CK_CUDA(cudaStreamSynchronize(s), "synchronise");
+    }
+    return CSRK_OK;
+}
+
+}  // namespace
+
+// ================================================================== C ABI
+extern "C" {
+
+int csrk_create(int32_t n, const int32_t* rowptr, const int32_t* colidx, const double* vals,
+                csrk_dtype dtype, csrk_handle* out) {
+    if (!out) return fail(CSRK_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (dtype != CSRK_F64 && dtype != CSRK_F32 && dtype != CSRK_BF16)
+        return fail(CSRK_ERR_ARG, "unknown dtype");
+    csrk_matrix* h = new (std::nothrow) csrk_matrix();
+    if (!h) return fail(CSRK_ERR_ALLOC, "out of host memory");
+    try {
+        std::string err;
+        int rc = ingest_csr(n, rowptr, colidx, vals, h->m, err);
+        if (rc) {
+            delete h;
+            return fail(rc, err);
+        }
+    } catch (const std::bad_alloc&) {
+        delete h;
+        return fail(CSRK_ERR_ALLOC, "out of host memory");
+    }
+    h->dtype = dtype;
+    *out = h;
+    return CSRK_OK;
+}
+
+int csrk_reorder(csrk_handle h, int method, int32_t* perm_out) {
+    if (!h) return fail(CSRK_ERR_ARG, "handle is NULL");
+    if (h->have_ptrs) return fail(CSRK_ERR_STATE, "reorder must come before csrk_set_sizes / csrk_set_pointers");
+    if (method != CSRK_REORDER_NONE && method != CSRK_REORDER_RCM) return fail(CSRK_ERR_ARG, "unknown method");
+    try {
+        if (method == CSRK_REORDER_RCM) {
+            std::vector<int32_t> local;   // permutation of the current form
+            rcm_permutation(h->m, local);
+            CsrHost b;
+            permute_symmetric(h->m, local, b);
+            h->m = std::move(b);
+            // a second reorder composes with the first: new -> previous -> input numbering
+            if (!h->perm.empty())
+                for (auto& p : local) p = h->perm[p];
+            h->perm = std::move(local);
+        }
+        if (perm_out) {
+            if (h->perm.empty())
+                for (int32_t i = 0; i < h->m.n; ++i) perm_out[i] = i;
+            else
+                std::memcpy(perm_out, h->perm.data(), sizeof(int32_t) * h->perm.size());
+        }
+    } catch (const std::bad_alloc&) {
+        return fail(CSRK_ERR_ALLOC, "out of host memory");
+    }
+    return CSRK_OK;
+}
+
+static int install_pointers(csrk_handle h, std::vector<int32_t>&& srp, std::vector<int32_t>&& ssrp) {
+    std::string err;
+    if (!check_pointers(h->m.n, srp, ssrp, err)) return fail(CSRK_ERR_ARG, err);
+    h->sr_ptr = std::move(srp);
+    h->ssr_ptr = std::move(ssrp);
+    build_descs(h->m, h->sr_ptr, h->ssr_ptr, h->desc, h->stats);
+    h->have_ptrs = true;
+    if (h->dev_struct) free_struct(h);   // pointer arrays changed: re-upload on next use
+    return CSRK_OK;
+}
+
+int csrk_set_sizes(csrk_handle h, int32_t sr, int32_t ssr) {
+    if (!h) return fail(CSRK_ERR_ARG, "handle is NULL");
+    if (sr == 0 && ssr == 0) return fail(CSRK_ERR_UNSUPPORTED, "autotuning is not available in this build");
+    if (sr <= 0 || ssr <= 0) return fail(CSRK_ERR_ARG, "sizes must be positive");
+    try {
+        std::vector<int32_t> srp, ssrp;
+        fixed_pointers(h->m.n, sr, ssr, srp, ssrp);
+        int rc = install_pointers(h, std::move(srp), std::move(ssrp));
+        if (rc) return rc;
+    } catch (const std::bad_alloc&) {
+        return fail(CSRK_ERR_ALLOC, "out of host memory");
+    }
+    h->sr = sr;
+    h->ssr = ssr;
+    return CSRK_OK;
+}
+
+int csrk_set_pointers(csrk_handle h, int32_t nsr, const int32_t* sr_ptr, int32_t nssr,
+                      const int32_t* ssr_ptr) {
+    if (!h) return fail(CSRK_ERR_ARG, "handle is NULL");
+    if (nsr < 0 || nssr < 0 || !sr_ptr || !ssr_ptr) return fail(CSRK_ERR_ARG, "bad pointer arrays");
+    try {
+        int rc = install_pointers(h, std::vector<int32_t>(sr_ptr, sr_ptr + nsr + 1),
+                                  std::vector<int32_t>(ssr_ptr, ssr_ptr + nssr + 1));
+        if (rc) return rc;
+    } catch (const std::bad_alloc&) {
+        return fail(CSRK_ERR_ALLOC, "out of host memory");
+    }
+    h->sr = h->ssr = 0;
+    return CSRK_OK;
+}
+
+int csrk_spmv(csrk_handle h, double alpha, const void* x, double beta, void* y, unsigned flags,
+              void* stream) {
+    return compute(h, 1, false, alpha, x, 1, beta, y, 1, flags, stream);
+}
+
+int csrk_spmm(csrk_handle h, int32_t k, double alpha, const void* X, int64_t ldx, double beta,
+              void* Y, int64_t ldy, unsigned flags, void* stream) {
+    if (k == 1 && ldx == 1 && ldy == 1) return compute(h, 1, false, alpha, X, 1, beta, Y, 1, flags, stream);
+    return compute(h, k, true, alpha, X, ldx, beta, Y, ldy, flags, stream);
+}
+
+int csrk_permute(csrk_handle h, int direction, int32_t k, const void* in, int64_t ldi, void* out,
+                 int64_t ldo, unsigned flags, void* stream) {
+    if (!h) return fail(CSRK_ERR_ARG, "handle is NULL");
+    if (!h->have_ptrs) return fail(CSRK_ERR_STATE, "call csrk_set_sizes or csrk_set_pointers first");
+    if (direction != 0 && direction != 1) return fail(CSRK_ERR_ARG, "direction must be 0 or 1");
+    if (k < 1 || ldi < k || ldo < k) return fail(CSRK_ERR_ARG, "bad k or leading dimension");
+    const int32_t n = h->m.n;
+    if (n > 0 && (!in || !out || in == out)) return fail(CSRK_ERR_ARG, "bad vector pointers");
+    int rc;
+    if ((rc = ensure_context(h))) return rc;
+    if ((rc = ensure_struct(h))) return rc;
+    if (n == 0) return CSRK_OK;
+    const int esz = (flags & CSRK_X_F32) ? 4 : 8;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (h->perm.empty()) {
+        CK_CUDA(cudaMemcpy2DAsync(out, (size_t)ldo * esz, in, (size_t)ldi * esz, (size_t)k * esz, n,
+                                  cudaMemcpyDeviceToDevice, s),
+                "copy");
+        return CSRK_OK;
+    }
+    int e = direction == 0 ? launch_gather_rows(in, ldi, out, ldo, h->d_perm, n, k, esz, s)
+                           : launch_scatter_rows(in, ldi, out, ldo, h->d_perm, n, k, esz, s);
+    if (e) return cuda_fail((cudaError_t)e, "permute");
+    return CSRK_OK;
+}
+
+int csrk_destroy(csrk_handle h) {
+    if (!h) return CSRK_OK;
+    if (h->device >= 0) {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (cur != h->device) cudaSetDevice(h->device);
+        cudaDeviceSynchronize();
+        free_device(h);
+        if (cur >= 0 && cur != h->device) cudaSetDevice(cur);
+    }
+    delete h;
+    return CSRK_OK;
+}
+
+int csrk_info(csrk_handle h, int32_t* n, int64_t* nnz, int32_t* nsr, int32_t* nssr, int32_t* sr,
+              int32_t* ssr, int32_t* dtype) {
+    if (!h) return fail(CSRK_ERR_ARG, "handle is NULL");
+    if (n) *n = h->m.n;
+    if (nnz) *nnz = h->m.nnz();
+    if (nsr) *nsr = h->have_ptrs ? (int32_t)h->sr_ptr.size() - 1 : 0;
+    if (nssr) *nssr = h->have_ptrs ? (int32_t)h->ssr_ptr.size() - 1 : 0;
+    if (sr) *sr = h->sr;
+    if (ssr) *ssr = h->ssr;
+    if (dtype) *dtype = (int32_t)h->dtype;
+    return CSRK_OK;
+}
+
+int csrk_export(csrk_handle h, int32_t* perm, int32_t* rowptr, int32_t* colidx, double* vals,
+                int32_t* sr_ptr, int32_t* ssr_ptr) {
+    if (!h) return fail(CSRK_ERR_ARG, "handle is NULL");
+    const CsrHost& m = h->m;
+    if (perm) {
+        if (h->perm.empty())
+            for (int32_t i = 0; i < m.n; ++i) perm[i] = i;
+        else
+            std::memcpy(perm, h->perm.data(), sizeof(int32_t) * m.n);
+    }
+    if (rowptr) std::memcpy(rowptr, m.rowptr.data(), sizeof(int32_t) * m.rowptr.size());
+    if (colidx && m.nnz()) std::memcpy(colidx, m.colidx.data(), sizeof(int32_t) * m.nnz());
+    if (vals && m.nnz()) std::memcpy(vals, m.vals.data(), sizeof(double) * m.nnz());
+    if ((sr_ptr || ssr_ptr) && !h->have_ptrs) return fail(CSRK_ERR_STATE, "pointer arrays not built yet");
+    if (sr_ptr) std::memcpy(sr_ptr, h->sr_ptr.data(), sizeof(int32_t) * h->sr_ptr.size());
+    if (ssr_ptr) std::memcpy(ssr_ptr, h->ssr_ptr.data(), sizeof(int32_t) * h->ssr_ptr.size());
+    return CSRK_OK;
+}
+
+int csrk_export_values(csrk_handle h, csrk_dtype dtype, void* out) {
+    if (!h || !out) return fail(CSRK_ERR_ARG, "NULL argument");
+    const int64_t nnz = h->m.nnz();
+    switch (dtype) {
+        case CSRK_F64: std::memcpy(out, h->m.vals.data(), sizeof(double) * nnz); return CSRK_OK;
+        case CSRK_F32: narrow_f32(h->m.vals.data(), static_cast<float*>(out), nnz); return CSRK_OK;
+        case CSRK_BF16: narrow_bf16(h->m.vals.data(), static_cast<uint16_t*>(out), nnz); return CSRK_OK;
+    }
+    return fail(CSRK_ERR_ARG, "unknown dtype");
+}
+
+int csrk_model_sizes(double rdensity, int arch, int32_t* ssrs, int32_t* srs) {
+    if (!(rdensity > 0) || !ssrs || !srs || (arch != 0 && arch != 1)) return fail(CSRK_ERR_ARG, "bad arguments");
+    // Sec. 4.1: log fit rounded half toward +infinity, then the rdensity case rules.
+    auto rnd = [](double v) { return (int32_t)std::floor(v + 0.5); };
+    const double lr = std::log(rdensity);
+    int32_t a, b;
+    const int c = rdensity <= 8 ? 1 : (rdensity <= 16 ? 2 : (rdensity <= 32 ? 3 : 4));
+    if (arch == 0) {
+        a = rnd(8.900 - 1.25 * lr);
+        b = rnd(10.146 - 1.50 * lr);
+        if (c == 2) { a = rnd(a * 1.5); b = b * 2; }
+        else if (c == 3) { a = a * 4; b = a / 2; }
+        else if (c == 4) { a = a * 5; b = a / 2; }
+    } else {
+        a = rnd(9.175 - 1.32 * lr);
+        b = rnd(20.500 - 3.50 * lr);
+        if (c == 2) { b = b * 4; }
+        else if (c == 3) { a = rnd(a * 2.5); b = a * 3; }
+        else if (c == 4) { a = a * 2; b = a * 2; }
+    }
+    *ssrs = a;
+    *srs = b;
+    return CSRK_OK;
+}
+
+int csrk_tuned_config(csrk_handle h, int32_t* kernel, int32_t* lanes, int32_t* warps,
+                      int32_t* stages, int32_t* ctas) {
+    if (!h) return fail(CSRK_ERR_ARG, "handle is NULL");
+    KernelConfig c = h->cfg;
+    if (!h->cfg_set) {
+        c = KernelConfig{};
+        c.lanes = default_lanes(h);
+    }
+    if (kernel) *kernel = c.kernel;
+    if (lanes) *lanes = c.lanes;
+    if (warps) *warps = c.warps;
+    if (stages) *stages = c.stages;
+    if (ctas) *ctas = c.ctas;
+    return CSRK_OK;
+}
+
+int csrk_set_config(csrk_handle h, int32_t kernel, int32_t lanes, int32_t warps, int32_t stages,
+                    int32_t ctas) {
+    if (!h) return fail(CSRK_ERR_ARG, "handle is NULL");
+    KernelConfig c = h->cfg;
+    if (!h->cfg_set) {
+        c = KernelConfig{};
+        c.lanes = default_lanes(h);
+    }
+    if (kernel >= 0) {
+        if (kernel > 1) return fail(CSRK_ERR_ARG, "kernel must be 0 or 1");
+        c.kernel = kernel;
+    }
+    if (lanes >= 0) {
+        if (lanes != 1 && lanes != 2 && lanes != 4 && lanes != 8 && lanes != 32)
+            return fail(CSRK_ERR_ARG, "lanes must be 1, 2, 4, 8 or 32");
+        c.lanes = lanes;
+    }
+    if (warps >= 0) {
+        if (warps < 1 || warps > 16) return fail(CSRK_ERR_ARG, "warps must be in [1, 16]");
+        c.warps = warps;
+    }
+    if (stages >= 0) {
+        if (stages == 1 || stages > 16) return fail(CSRK_ERR_ARG, "stages must be 0 or in [2, 16]");
+        c.stages = stages;
+    }
+    if (ctas >= 0) {
+        if (ctas < 1 || ctas > 4) return fail(CSRK_ERR_ARG, "ctas must be in [1, 4]");
+        c.ctas = ctas;
+    }
+    h->cfg = c;
+    h->cfg_set = true;
+    return CSRK_OK;
+}
+
+int csrk_device_status(csrk_handle h, void* stream, int32_t* status) {
+    if (!h || !status) return fail(CSRK_ERR_ARG, "NULL argument");
+    *status = 0;
+    if (h->device < 0) return CSRK_OK;
+    CK_CUDA(cudaStreamSynchronize((cudaStream_t)stream), "synchronise");
+    CK_CUDA(cudaMemcpy(status, h->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost), "read status");
+    CK_CUDA(cudaMemset(h->d_status, 0, sizeof(int32_t)), "clear status");
+    if (*status) return fail(CSRK_ERR_TIMEOUT, "a device-side bounded wait ran out");
+    return CSRK_OK;
+}
+
+const char* csrk_last_error(void) { return g_last_error.c_str(); }
+
+const char* csrk_build_info(void) {
+    return "csrk: sm_103a; CSR-3 TMA (cp.async.bulk + mbarrier) and direct kernels; "
+           "values f64/f32/bf16";
+}
+
+}  // extern "C"

@@ -1,0 +1,116 @@
+// Internal declarations of the CSR-k library (not part of the C ABI).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "csrk.h"
+
+namespace csrk {
+
+// ------------------------------------------------------------------ host CSR
+struct CsrHost {
+    int32_t n = 0;
+    std::vector<int32_t> rowptr;   // n + 1
+    std::vector<int32_t> colidx;   // nnz
+    std::vector<double> vals;      // nnz
+    int64_t nnz() const { return rowptr.empty() ? 0 : rowptr.back(); }
+};
+
+// Per super-super-row work descriptor, derived from ssr_ptr / sr_ptr / rowptr so that a
+// kernel learns an SSR's super-row, row and nonzero ranges with one 32-byte load instead
+// of three dependent ones.  Not part of the CSR-k format itself.
+struct alignas(16) SsrDesc {
+    int32_t s0, s1;   // super-rows [s0, s1)
+    int32_t r0, r1;   // rows [r0, r1)
+    int32_t p0, p1;   // nonzeros [p0, p1)
+    int32_t pad0, pad1;
+};
+
+struct TileStats {
+    int32_t max_srs = 0;    // most super-rows in one SSR
+    int32_t max_rows = 0;   // most rows in one SSR
+    int64_t max_nnz = 0;    // most nonzeros in one SSR
+    int32_t max_sr_rows = 0;
+    int32_t max_row_len = 0;
+};
+
+// host_builder.cpp -------------------------------------------------------------
+// Validate a CSR matrix and copy it with each row's columns ascending.  Returns
+// CSRK_OK or CSRK_ERR_MATRIX / CSRK_ERR_ARG with a message in err.
+int ingest_csr(int32_t n, const int32_t* rowptr, const int32_t* colidx, const double* vals,
+               CsrHost& out, std::string& err);
+// Reverse Cuthill-McKee permutation, perm[new] = old.
+void rcm_permutation(const CsrHost& a, std::vector<int32_t>& perm);
+// B = P A P^T, rows' columns ascending.
+void permute_symmetric(const CsrHost& a, const std::vector<int32_t>& perm, CsrHost& b);
+void fixed_pointers(int32_t n, int32_t sr, int32_t ssr, std::vector<int32_t>& sr_ptr,
+                    std::vector<int32_t>& ssr_ptr);
+bool check_pointers(int32_t n, const std::vector<int32_t>& sr_ptr,
+                    const std::vector<int32_t>& ssr_ptr, std::string& err);
+void build_descs(const CsrHost& b, const std::vector<int32_t>& sr_ptr,
+                 const std::vector<int32_t>& ssr_ptr, std::vector<SsrDesc>& desc,
+                 TileStats& st);
+void narrow_f32(const double* in, float* out, int64_t n);
+void narrow_bf16(const double* in, uint16_t* out, int64_t n);
+uint16_t f64_to_bf16(double d);
+void parallel_for(int64_t n, int64_t grain, void (*fn)(int64_t, int64_t, void*), void* ctx);
+
+// ------------------------------------------------------------------ launches
+enum ValType { VAL_F64 = 0, VAL_F32 = 1, VAL_BF16 = 2 };
+
+struct KernelConfig {
+    int kernel = 0;    // 0 TMA-staged, 1 direct loads
+    int lanes = 1;     // lanes per row (SpMV)
+    int warps = 8;     // consumer warps per CTA
+    int stages = 0;    // 0 = as many as fit
+    int ctas = 1;      // CTAs per SM
+};
+
+// Arguments of one SpMV / SpMM launch over the device CSR-k form.
+struct LaunchArgs {
+    const SsrDesc* desc;
+    const int32_t* sr_ptr;
+    const int32_t* rowptr;
+    const int32_t* colidx;
+    const void* vals;
+    const void* x;
+    void* y;
+    int64_t ldx, ldy;
+    int32_t k;          // right-hand sides (1 for SpMV)
+    int32_t nssr;
+    double alpha, beta;
+    int32_t* status;
+    TileStats stats;
+    int val_type;       // ValType
+    bool x_f32;
+    bool acc_f32;
+    bool spmm;
+    int num_sms;
+    unsigned long long timeout_ns;
+};
+
+// Shared-memory plan of the TMA kernel for one value type.
+struct StagePlan {
+    uint32_t off_srp, off_rp, off_col, off_val, stage_bytes, header_bytes;
+    int stages;
+};
+bool plan_stages(const TileStats& st, int val_bytes, int max_smem, int want_stages,
+                 StagePlan& plan);
+
+// spmv_*.cu: launch on `stream`; returns a cudaError_t value (0 = success) or -1 when the
+// combination is not compiled in.
+int launch_csr3(const LaunchArgs& a, const KernelConfig& cfg, const StagePlan& plan,
+                void* stream);
+int launch_csr3_f64(const LaunchArgs& a, const KernelConfig& cfg, const StagePlan& plan, void* stream);
+int launch_csr3_f32(const LaunchArgs& a, const KernelConfig& cfg, const StagePlan& plan, void* stream);
+int launch_csr3_bf16(const LaunchArgs& a, const KernelConfig& cfg, const StagePlan& plan, void* stream);
+
+// vec_kernels.cu
+int launch_gather_rows(const void* in, int64_t ldi, void* out, int64_t ldo, const int32_t* perm,
+                       int32_t n, int32_t k, int elem_bytes, void* stream);
+int launch_scatter_rows(const void* in, int64_t ldi, void* out, int64_t ldo, const int32_t* perm,
+                        int32_t n, int32_t k, int elem_bytes, void* stream);
+
+}  // namespace csrk

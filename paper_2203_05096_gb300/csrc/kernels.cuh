@@ -1,0 +1,385 @@
+// CSR-3 SpMV / SpMM kernels for sm_103a.
+//
+// Mapping (Sec. 3's GPU view of CSR-3, re-designed for GB300):
+//   * one super-super-row (SSR) at a time per thread block; the blocks are persistent
+//     and walk the SSRs blockIdx.x, blockIdx.x + gridDim.x, ...
+//   * the block's consumer warps share the stream of super-rows (SR) of those SSRs:
+//     warp w takes every W-th SR, so an SR is handled by one warp (the paper's y level);
+//   * inside an SR, `LPR` lanes cooperate on one row (LPR = 1 is GPU-SpMV-3's row per
+//     thread, LPR > 1 is GPU-SpMV-3.5's lanes across a row, reduced with warp shuffles
+//     instead of a shared-memory tree);
+//   * SpMM: `G` lanes share a row and split its right-hand-side columns.
+// Because an SSR's rows are contiguous, its sr_ptr, rowptr, colidx and vals slices are
+// four contiguous byte ranges.  In the TMA kernel a producer warp copies them into a
+// ring of shared-memory stages with cp.async.bulk (completion counted by an mbarrier,
+// L2 evict-first hint so that x stays resident in L2), S-1 SSRs ahead of the consumers.
+// x is gathered through the read-only path; y is written once per row.
+//
+// GB300 note: FP64 FMA runs at about 2 per clock per SM here, so the FP64 path spends
+// exactly one FP64 instruction per nonzero: narrow values are widened with integer
+// instructions (a float->double conversion would also occupy the FP64 pipe) and the
+// row-per-lane mapping needs no FP64 shuffle reduction.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "csrk_internal.h"
+
+namespace csrk {
+namespace dev {
+
+// ------------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(
+                     smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Wait for the phase with the given parity to complete, giving up after timeout_ns.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
+                                                  unsigned long long timeout_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (uint32_t it = 1;; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 63u) == 0 && global_ns() - t0 > timeout_ns) return false;
+    }
+}
+__device__ __forceinline__ uint64_t policy_evict_first() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+// 1-D bulk copy global -> shared, completion reported to `bar` in bytes.  dst, src and
+// bytes must be multiples of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar, uint64_t policy) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+        " [%0], [%1], %2, [%3], %4;" ::"r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(policy)
+        : "memory");
+}
+
+// ------------------------------------------------------------------ value widening
+// FP32 bit pattern -> FP64 with integer instructions only (exact for every input).
+__device__ __forceinline__ double f32bits_to_f64(uint32_t u) {
+    const uint64_t sign = (uint64_t)(u & 0x80000000u) << 32;
+    const uint32_t e = (u >> 23) & 0xFFu;
+    const uint32_t m = u & 0x7FFFFFu;
+    uint64_t bits;
+    if (e - 1u < 254u) {   // normal
+        bits = sign | ((uint64_t)(e + 896u) << 52) | ((uint64_t)m << 29);
+    } else if (e == 0xFFu) {   // Inf / NaN
+        bits = sign | 0x7FF0000000000000ull | ((uint64_t)m << 29);
+    } else if (m == 0) {   // zero
+        bits = sign;
+    } else {   // FP32 subnormal: m * 2^-149, normalise
+        const int top = 31 - __clz(m);   // 0..22
+        const uint64_t frac = (uint64_t)(m ^ (1u << top)) << (52 - top);
+        bits = sign | ((uint64_t)(top + 874) << 52) | frac;
+    }
+    return __longlong_as_double((long long)bits);
+}
+
+template <typename VT> struct Val;
+template <> struct Val<double> {
+    static constexpr int bytes = 8;
+    __device__ __forceinline__ static double f64(double v) { return v; }
+    __device__ __forceinline__ static float f32(double v) { return (float)v; }
+};
+template <> struct Val<float> {
+    static constexpr int bytes = 4;
+    __device__ __forceinline__ static double f64(float v) { return f32bits_to_f64(__float_as_uint(v)); }
+    __device__ __forceinline__ static float f32(float v) { return v; }
+};
+// BF16 values travel as their 16-bit pattern.
+struct bf16_t { uint16_t bits; };
+template <> struct Val<bf16_t> {
+    static constexpr int bytes = 2;
+    __device__ __forceinline__ static double f64(bf16_t v) { return f32bits_to_f64((uint32_t)v.bits << 16); }
+    __device__ __forceinline__ static float f32(bf16_t v) { return __uint_as_float((uint32_t)v.bits << 16); }
+};
+
+__device__ __forceinline__ double x_f64(double x) { return x; }
+__device__ __forceinline__ double x_f64(float x) { return f32bits_to_f64(__float_as_uint(x)); }
+
+template <typename AT> struct Acc;
+template <> struct Acc<double> {
+    template <typename VT, typename XT>
+    __device__ __forceinline__ static double fma(VT v, XT x, double s) {
+        return ::fma(Val<VT>::f64(v), x_f64(x), s);
+    }
+};
+template <> struct Acc<float> {
+    template <typename VT, typename XT>
+    __device__ __forceinline__ static float fma(VT v, XT x, float s) {
+        return fmaf(Val<VT>::f32(v), (float)x, s);
+    }
+};
+
+template <typename T>
+__device__ __forceinline__ T ldg_x(const T* p) { return __ldg(p); }
+
+__device__ __forceinline__ void report(int32_t* status, int32_t bit) {
+    if (status) atomicOr(status, bit);
+}
+
+// y = alpha*acc + beta*y in the accumulation precision; beta == 0 never reads y.
+template <typename XT, typename AT>
+__device__ __forceinline__ void store_y(XT* y, int64_t idx, AT acc, double alpha, double beta) {
+    if constexpr (sizeof(AT) == 8) {
+        double r = alpha * acc;
+        if (beta != 0.0) r = fma(beta, x_f64(y[idx]), r);
+        y[idx] = (XT)r;
+    } else {
+        float r = (float)alpha * acc;
+        if (beta != 0.0) r = fmaf((float)beta, (float)y[idx], r);
+        y[idx] = (XT)r;
+    }
+}
+
+// ------------------------------------------------------------------ row compute
+// One pass of a warp over up to 32/LPR rows [rb + lane/LPR ...] of a super-row.
+// col_s / val_s are indexable by absolute nonzero index (already offset).
+template <typename VT, typename XT, typename AT, int LPR>
+__device__ __forceinline__ void spmv_rows(int rb, int re, const int32_t* __restrict__ rp,
+                                          const int32_t* __restrict__ col_s,
+                                          const VT* __restrict__ val_s,
+                                          const XT* __restrict__ x, XT* __restrict__ y,
+                                          double alpha, double beta, int lane) {
+    constexpr int RPP = 32 / LPR;   // rows per pass
+    const int sub = lane % LPR;
+    for (int base = rb; base < re; base += RPP) {
+        const int r = base + lane / LPR;
+        AT acc = 0;
+        if (r < re) {
+            const int pb = rp[r], pe = rp[r + 1];
+            int p = pb + sub;
+#pragma unroll 4
+            for (; p < pe; p += LPR) acc = Acc<AT>::fma(val_s[p], ldg_x(&x[col_s[p]]), acc);
+        }
+        if constexpr (LPR > 1) {
+#pragma unroll
+            for (int off = LPR / 2; off > 0; off >>= 1)
+                acc += __shfl_xor_sync(0xffffffffu, acc, off);
+        }
+        if (r < re && sub == 0) store_y<XT, AT>(y, r, acc, alpha, beta);
+    }
+}
+
+// SpMM pass: G lanes per row, lane c0 = lane % G owns columns c0, c0+G, ... (< k, CPL of
+// them).  X, Y row-major with leading dimensions ldx, ldy.
+template <typename VT, typename XT, typename AT, int G, int CPL>
+__device__ __forceinline__ void spmm_rows(int rb, int re, const int32_t* __restrict__ rp,
+                                          const int32_t* __restrict__ col_s,
+                                          const VT* __restrict__ val_s,
+                                          const XT* __restrict__ X, int64_t ldx,
+                                          XT* __restrict__ Y, int64_t ldy, int k,
+                                          double alpha, double beta, int lane) {
+    constexpr int RPP = 32 / G;
+    const int c0 = lane % G;
+    for (int base = rb; base < re; base += RPP) {
+        const int r = base + lane / G;
+        if (r >= re) continue;
+        AT acc[CPL];
+#pragma unroll
+        for (int j = 0; j < CPL; ++j) acc[j] = 0;
+        const int pb = rp[r], pe = rp[r + 1];
+#pragma unroll 2
+        for (int p = pb; p < pe; ++p) {
+            const VT v = val_s[p];
+            const XT* xr = X + (int64_t)col_s[p] * ldx;
+#pragma unroll
+            for (int j = 0; j < CPL; ++j) {
+                const int c = c0 + j * G;
+                if (c < k) acc[j] = Acc<AT>::fma(v, ldg_x(&xr[c]), acc[j]);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < CPL; ++j) {
+            const int c = c0 + j * G;
+            if (c < k) store_y<XT, AT>(Y + (int64_t)r * ldy, c, acc[j], alpha, beta);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ TMA kernel
+struct TmaParams {
+    const SsrDesc* desc;
+    const int32_t* sr_ptr;
+    const int32_t* rowptr;
+    const int32_t* colidx;
+    const void* vals;
+    const void* x;
+    void* y;
+    int64_t ldx, ldy;
+    int32_t k;
+    int32_t nssr;
+    double alpha, beta;
+    int32_t* status;
+    uint32_t off_srp, off_rp, off_col, off_val, stage_bytes, header_bytes;
+    int32_t stages;
+    unsigned long long timeout_ns;
+};
+
+// Byte range [b, e) of an element slice rounded out to 16-byte boundaries.
+template <int ESZ>
+__device__ __forceinline__ void slice16(int64_t first, int64_t last_excl, int64_t& a0, uint32_t& bytes) {
+    constexpr int64_t per = 16 / ESZ;
+    a0 = first & ~(per - 1);
+    const int64_t a1 = (last_excl + per - 1) & ~(per - 1);
+    bytes = (uint32_t)((a1 - a0) * ESZ);
+}
+
+// MODE 0: SpMV with LPR lanes per row.  MODE 1: SpMM with G = LPR lanes per row and CPL
+// columns per lane.
+template <typename VT, typename XT, typename AT, int LPR, int MODE, int CPL>
+__global__ void __launch_bounds__(544, 1) csr3_tma_kernel(const TmaParams P) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int S = P.stages;
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem);
+    uint64_t* empty = full + S;
+    SsrDesc* dsc = reinterpret_cast<SsrDesc*>(smem + 16 * S);   // one per stage
+    unsigned char* stage0 = smem + P.header_bytes;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int W = (blockDim.x >> 5) - 1;   // consumer warps; the last warp produces
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], W);
+        }
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    if (warp == W) {
+        // ---------------- producer: one elected lane issues the bulk copies
+        if (lane == 0) {
+            const uint64_t pol = policy_evict_first();
+            int i = 0;
+            for (int t = blockIdx.x; t < P.nssr; t += gridDim.x, ++i) {
+                const int s = i % S;
+                if (i >= S && !mbar_wait_bounded(&empty[s], ((i / S) - 1) & 1, P.timeout_ns)) {
+                    report(P.status, 1);
+                    break;
+                }
+                const SsrDesc d = P.desc[t];
+                dsc[s] = d;
+                unsigned char* st = stage0 + (size_t)s * P.stage_bytes;
+                int64_t a0;
+                uint32_t b_srp, b_rp, b_col, b_val;
+                int64_t o_srp, o_rp, o_col, o_val;
+                slice16<4>(d.s0, (int64_t)d.s1 + 1, o_srp, b_srp);
+                slice16<4>(d.r0, (int64_t)d.r1 + 1, o_rp, b_rp);
+                slice16<4>(d.p0, d.p1, o_col, b_col);
+                slice16<sizeof(VT)>(d.p0, d.p1, o_val, b_val);
+                (void)a0;
+                mbar_arrive_expect_tx(&full[s], b_srp + b_rp + b_col + b_val);
+                bulk_g2s(st + P.off_srp, P.sr_ptr + o_srp, b_srp, &full[s], pol);
+                bulk_g2s(st + P.off_rp, P.rowptr + o_rp, b_rp, &full[s], pol);
+                if (b_col) bulk_g2s(st + P.off_col, P.colidx + o_col, b_col, &full[s], pol);
+                if (b_val)
+                    bulk_g2s(st + P.off_val, static_cast<const VT*>(P.vals) + o_val, b_val,
+                             &full[s], pol);
+            }
+        }
+        return;
+    }
+
+    // ---------------- consumers
+    const XT* __restrict__ x = static_cast<const XT*>(P.x);
+    XT* __restrict__ y = static_cast<XT*>(P.y);
+    int i = 0;
+    int sr_seq = 0;   // index of the next super-row in this block's stream
+    for (int t = blockIdx.x; t < P.nssr; t += gridDim.x, ++i) {
+        const int s = i % S;
+        if (!mbar_wait_bounded(&full[s], (i / S) & 1, P.timeout_ns)) {
+            report(P.status, 1);
+            // wait once more, bounded, for the copies of this stage to land before leaving
+            mbar_wait_bounded(&full[s], (i / S) & 1, P.timeout_ns);
+            return;
+        }
+        const SsrDesc d = dsc[s];
+        const unsigned char* st = stage0 + (size_t)s * P.stage_bytes;
+        const int32_t* srp = reinterpret_cast<const int32_t*>(st + P.off_srp) - (d.s0 & ~3);
+        const int32_t* rp = reinterpret_cast<const int32_t*>(st + P.off_rp) - (d.r0 & ~3);
+        const int32_t* col = reinterpret_cast<const int32_t*>(st + P.off_col) - (d.p0 & ~3);
+        constexpr int VPER = 16 / (int)sizeof(VT);
+        const VT* val = reinterpret_cast<const VT*>(st + P.off_val) - (d.p0 & ~(VPER - 1));
+        const int nsr = d.s1 - d.s0;
+        // super-rows of this SSR that fall to this warp in the block-wide stream
+        int first = (warp - sr_seq % W + W) % W;
+        for (int j = first; j < nsr; j += W) {
+            const int sr = d.s0 + j;
+            const int rb = srp[sr], re = srp[sr + 1];
+            if constexpr (MODE == 0)
+                spmv_rows<VT, XT, AT, LPR>(rb, re, rp, col, val, x, y, P.alpha, P.beta, lane);
+            else
+                spmm_rows<VT, XT, AT, LPR, CPL>(rb, re, rp, col, val, x, P.ldx, y, P.ldy, P.k,
+                                                 P.alpha, P.beta, lane);
+        }
+        sr_seq += nsr;
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);
+    }
+}
+
+// ------------------------------------------------------------------ direct kernel
+// One block per SSR (the paper's 1-D grid), consumer warps stride the SSR's super-rows,
+// operands read straight from global memory.  Used when an SSR does not fit a stage and
+// as an autotuner alternative.
+template <typename VT, typename XT, typename AT, int LPR, int MODE, int CPL>
+__global__ void __launch_bounds__(512, 1) csr3_direct_kernel(const TmaParams P) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int W = blockDim.x >> 5;
+    const XT* __restrict__ x = static_cast<const XT*>(P.x);
+    XT* __restrict__ y = static_cast<XT*>(P.y);
+    const VT* __restrict__ vals = static_cast<const VT*>(P.vals);
+    for (int t = blockIdx.x; t < P.nssr; t += gridDim.x) {
+        const SsrDesc d = P.desc[t];
+        for (int sr = d.s0 + warp; sr < d.s1; sr += W) {
+            const int rb = __ldg(&P.sr_ptr[sr]), re = __ldg(&P.sr_ptr[sr + 1]);
+            if constexpr (MODE == 0)
+                spmv_rows<VT, XT, AT, LPR>(rb, re, P.rowptr, P.colidx, vals, x, y, P.alpha,
+                                           P.beta, lane);
+            else
+                spmm_rows<VT, XT, AT, LPR, CPL>(rb, re, P.rowptr, P.colidx, vals, x, P.ldx, y,
+                                                 P.ldy, P.k, P.alpha, P.beta, lane);
+        }
+    }
+}
+
+}  // namespace dev
+}  // namespace csrk

@@ -1,0 +1,89 @@
+// Instantiation and launch of the CSR-3 kernels for one stored value type.  Each value
+// type lives in its own translation unit (spmv_f64.cu, spmv_f32.cu, spmv_bf16.cu) so the
+// template instances compile in parallel.
+#pragma once
+
+#include "kernels.cuh"
+
+namespace csrk {
+namespace dev {
+
+template <typename VT, typename XT, typename AT, int LPR, int MODE, int CPL>
+static int launch_one(const LaunchArgs& a, const KernelConfig& cfg, const StagePlan& plan,
+                      cudaStream_t stream) {
+    TmaParams P;
+    P.desc = a.desc;
+    P.sr_ptr = a.sr_ptr;
+    P.rowptr = a.rowptr;
+    P.colidx = a.colidx;
+    P.vals = a.vals;
+    P.x = a.x;
+    P.y = a.y;
+    P.ldx = a.ldx;
+    P.ldy = a.ldy;
+    P.k = a.k;
+    P.nssr = a.nssr;
+    P.alpha = a.alpha;
+    P.beta = a.beta;
+    P.status = a.status;
+    P.off_srp = plan.off_srp;
+    P.off_rp = plan.off_rp;
+    P.off_col = plan.off_col;
+    P.off_val = plan.off_val;
+    P.stage_bytes = plan.stage_bytes;
+    P.header_bytes = plan.header_bytes;
+    P.stages = plan.stages;
+    P.timeout_ns = a.timeout_ns;
+    if (a.nssr == 0) return 0;
+    if (cfg.kernel == 0) {
+        auto kern = csr3_tma_kernel<VT, XT, AT, LPR, MODE, CPL>;
+        const int smem = (int)(plan.header_bytes + (size_t)plan.stages * plan.stage_bytes);
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return (int)e;
+        const int threads = 32 * (cfg.warps + 1);
+        int grid = a.num_sms * cfg.ctas;
+        if (grid > a.nssr) grid = a.nssr;
+        kern<<<grid, threads, smem, stream>>>(P);
+    } else {
+        auto kern = csr3_direct_kernel<VT, XT, AT, LPR, MODE, CPL>;
+        const int threads = 32 * cfg.warps;
+        int grid = a.nssr;
+        kern<<<grid, threads, 0, stream>>>(P);
+    }
+    return (int)cudaGetLastError();
+}
+
+template <typename VT, typename XT, typename AT>
+static int dispatch_lanes(const LaunchArgs& a, const KernelConfig& cfg, const StagePlan& plan,
+                          cudaStream_t s) {
+    if (!a.spmm) {
+        if (cfg.kernel == 0) {
+            switch (cfg.lanes) {
+                case 1: return launch_one<VT, XT, AT, 1, 0, 1>(a, cfg, plan, s);
+                case 2: return launch_one<VT, XT, AT, 2, 0, 1>(a, cfg, plan, s);
+                case 4: return launch_one<VT, XT, AT, 4, 0, 1>(a, cfg, plan, s);
+                case 8: return launch_one<VT, XT, AT, 8, 0, 1>(a, cfg, plan, s);
+                case 32: return launch_one<VT, XT, AT, 32, 0, 1>(a, cfg, plan, s);
+                default: return -1;
+            }
+        }
+        switch (cfg.lanes) {
+            case 1: return launch_one<VT, XT, AT, 1, 0, 1>(a, cfg, plan, s);
+            case 4: return launch_one<VT, XT, AT, 4, 0, 1>(a, cfg, plan, s);
+            case 32: return launch_one<VT, XT, AT, 32, 0, 1>(a, cfg, plan, s);
+            default: return -1;
+        }
+    }
+    // SpMM: G lanes per row, columns split across them, at most 2 per lane.
+    const int k = a.k;
+    if (k <= 2) return launch_one<VT, XT, AT, 2, 1, 1>(a, cfg, plan, s);
+    if (k <= 4) return launch_one<VT, XT, AT, 4, 1, 1>(a, cfg, plan, s);
+    if (k <= 8) return launch_one<VT, XT, AT, 8, 1, 1>(a, cfg, plan, s);
+    if (k <= 16) return launch_one<VT, XT, AT, 16, 1, 1>(a, cfg, plan, s);
+    if (k <= 32) return launch_one<VT, XT, AT, 32, 1, 1>(a, cfg, plan, s);
+    if (k <= 64) return launch_one<VT, XT, AT, 32, 1, 2>(a, cfg, plan, s);
+    return -1;
+}
+
+}  // namespace dev
+}  // namespace csrk

@@ -1,0 +1,242 @@
+"""Thin Python binding of the C ABI in include/csrk.h (argument marshalling only).
+
+Every function here has the C entry point's name without the ``csrk_`` prefix and does
+nothing but convert arguments: numpy arrays become host pointers, torch tensors device
+pointers, ``stream=None`` becomes the current torch stream of the tensors' device.  All
+computation runs in libcsrk.so; if the library is missing or fails to load, ``lib()``
+raises -- there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_LIB = None
+
+F64, F32, BF16 = 0, 1, 2
+DTYPES = {"f64": F64, "f32": F32, "bf16": BF16, F64: F64, F32: F32, BF16: BF16}
+VEC_PERMUTED, ACC_F32, X_F32, HOST_VECTORS = 1, 2, 4, 8
+REORDER = {"none": 0, "rcm": 1, 0: 0, 1: 1}
+STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_MATRIX", 3: "ERR_STATE", 4: "ERR_ALLOC",
+          5: "ERR_CUDA", 6: "ERR_UNSUPPORTED", 7: "ERR_TIMEOUT", 8: "ERR_NOT_CONVERGED"}
+
+
+class CsrkError(RuntimeError):
+    def __init__(self, code: int, message: str, func: str):
+        self.code = code
+        self.status = STATUS.get(code, str(code))
+        super().__init__(f"{func}: {self.status}: {message}")
+
+
+_vp = ctypes.c_void_p
+_i32 = ctypes.c_int32
+_i64 = ctypes.c_int64
+_d = ctypes.c_double
+_u = ctypes.c_uint
+_pi32 = ctypes.POINTER(ctypes.c_int32)
+_pi64 = ctypes.POINTER(ctypes.c_int64)
+
+_PROTOS = {
+    "csrk_create": [_i32, _vp, _vp, _vp, ctypes.c_int, ctypes.POINTER(_vp)],
+    "csrk_reorder": [_vp, ctypes.c_int, _vp],
+    "csrk_set_sizes": [_vp, _i32, _i32],
+    "csrk_set_pointers": [_vp, _i32, _vp, _i32, _vp],
+    "csrk_spmv": [_vp, _d, _vp, _d, _vp, _u, _vp],
+    "csrk_spmm": [_vp, _i32, _d, _vp, _i64, _d, _vp, _i64, _u, _vp],
+    "csrk_destroy": [_vp],
+    "csrk_permute": [_vp, ctypes.c_int, _i32, _vp, _i64, _vp, _i64, _u, _vp],
+    "csrk_info": [_vp, _pi32, _pi64, _pi32, _pi32, _pi32, _pi32, _pi32],
+    "csrk_export": [_vp, _vp, _vp, _vp, _vp, _vp, _vp],
+    "csrk_export_values": [_vp, ctypes.c_int, _vp],
+    "csrk_model_sizes": [_d, ctypes.c_int, _pi32, _pi32],
+    "csrk_tuned_config": [_vp, _pi32, _pi32, _pi32, _pi32, _pi32],
+    "csrk_set_config": [_vp, _i32, _i32, _i32, _i32, _i32],
+    "csrk_device_status": [_vp, _vp, _pi32],
+}
+
+
+def lib(build_if_missing: bool = True):
+    """Load libcsrk.so (building it first when the sources are newer)."""
+    global _LIB
+    if _LIB is None:
+        path = _build.LIB
+        if build_if_missing:
+            path = _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError(f"libcsrk.so not found at {path}; run __graft_entry__.build()")
+        h = ctypes.CDLL(path)
+        for name, args in _PROTOS.items():
+            fn = getattr(h, name)
+            fn.argtypes = args
+            fn.restype = ctypes.c_int
+        h.csrk_last_error.argtypes = []
+        h.csrk_last_error.restype = ctypes.c_char_p
+        h.csrk_build_info.argtypes = []
+        h.csrk_build_info.restype = ctypes.c_char_p
+        _LIB = h
+    return _LIB
+
+
+def _check(rc: int, func: str):
+    if rc != 0:
+        msg = lib().csrk_last_error().decode(errors="replace")
+        raise CsrkError(rc, msg, func)
+
+
+def _host(a, dtype):
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    return arr, arr.ctypes.data_as(_vp)
+
+
+def _ptr(t):
+    """Device (torch tensor) or host (numpy array) pointer of a vector argument."""
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        if not t.flags["C_CONTIGUOUS"]:
+            raise ValueError("host vectors must be C-contiguous")
+        return t.ctypes.data
+    if hasattr(t, "data_ptr"):
+        return t.data_ptr()
+    return int(t)
+
+
+def _stream(stream, *tensors):
+    if stream is not None:
+        return int(stream) if not hasattr(stream, "cuda_stream") else stream.cuda_stream
+    for t in tensors:
+        if hasattr(t, "is_cuda") and t.is_cuda:
+            import torch
+            return torch.cuda.current_stream(t.device).cuda_stream
+    return None
+
+
+# ------------------------------------------------------------------ entry points
+def create(n, rowptr, colidx, vals, dtype="f64"):
+    rp, prp = _host(rowptr, np.int32)
+    ci, pci = _host(colidx, np.int32)
+    va, pva = _host(vals, np.float64)
+    if rp.size != n + 1:
+        raise ValueError("rowptr must have n + 1 entries")
+    out = _vp()
+    _check(lib().csrk_create(int(n), prp, pci, pva, DTYPES[dtype], ctypes.byref(out)), "csrk_create")
+    return out.value
+
+
+def reorder(h, method="rcm", want_perm=True):
+    n = info(h)["n"]
+    perm = np.empty(n, dtype=np.int32) if want_perm else None
+    _check(lib().csrk_reorder(h, REORDER[method], None if perm is None else perm.ctypes.data_as(_vp)),
+           "csrk_reorder")
+    return perm
+
+
+def set_sizes(h, sr, ssr):
+    _check(lib().csrk_set_sizes(h, int(sr), int(ssr)), "csrk_set_sizes")
+
+
+def set_pointers(h, sr_ptr, ssr_ptr):
+    a, pa = _host(sr_ptr, np.int32)
+    b, pb = _host(ssr_ptr, np.int32)
+    _check(lib().csrk_set_pointers(h, a.size - 1, pa, b.size - 1, pb), "csrk_set_pointers")
+
+
+def spmv(h, alpha, x, beta, y, flags=0, stream=None):
+    _check(lib().csrk_spmv(h, float(alpha), _ptr(x), float(beta), _ptr(y), int(flags),
+                           _stream(stream, x, y)), "csrk_spmv")
+
+
+def spmm(h, k, alpha, X, ldx, beta, Y, ldy, flags=0, stream=None):
+    _check(lib().csrk_spmm(h, int(k), float(alpha), _ptr(X), int(ldx), float(beta), _ptr(Y),
+                           int(ldy), int(flags), _stream(stream, X, Y)), "csrk_spmm")
+
+
+def permute(h, direction, k, inp, ldi, out, ldo, flags=0, stream=None):
+    _check(lib().csrk_permute(h, int(direction), int(k), _ptr(inp), int(ldi), _ptr(out), int(ldo),
+                              int(flags), _stream(stream, inp, out)), "csrk_permute")
+
+
+def destroy(h):
+    if h:
+        _check(lib().csrk_destroy(h), "csrk_destroy")
+
+
+def info(h):
+    v = [ctypes.c_int32() for _ in range(6)]
+    nnz = ctypes.c_int64()
+    _check(lib().csrk_info(h, ctypes.byref(v[0]), ctypes.byref(nnz), ctypes.byref(v[1]),
+                           ctypes.byref(v[2]), ctypes.byref(v[3]), ctypes.byref(v[4]),
+                           ctypes.byref(v[5])), "csrk_info")
+    return dict(n=v[0].value, nnz=nnz.value, nsr=v[1].value, nssr=v[2].value, sr=v[3].value,
+                ssr=v[4].value, dtype=v[5].value)
+
+
+def export(h, with_pointers=True):
+    d = info(h)
+    n, nnz = d["n"], d["nnz"]
+    perm = np.empty(n, np.int32)
+    rowptr = np.empty(n + 1, np.int32)
+    colidx = np.empty(nnz, np.int32)
+    vals = np.empty(nnz, np.float64)
+    srp = np.empty(d["nsr"] + 1, np.int32) if with_pointers else None
+    ssrp = np.empty(d["nssr"] + 1, np.int32) if with_pointers else None
+    p = lambda a: None if a is None else a.ctypes.data_as(_vp)
+    _check(lib().csrk_export(h, p(perm), p(rowptr), p(colidx), p(vals), p(srp), p(ssrp)), "csrk_export")
+    return dict(perm=perm, rowptr=rowptr, colidx=colidx, vals=vals, sr_ptr=srp, ssr_ptr=ssrp)
+
+
+def export_values(h, dtype):
+    nnz = info(h)["nnz"]
+    dt = {F64: np.float64, F32: np.float32, BF16: np.uint16}[DTYPES[dtype]]
+    out = np.empty(nnz, dt)
+    _check(lib().csrk_export_values(h, DTYPES[dtype], out.ctypes.data_as(_vp)), "csrk_export_values")
+    return out
+
+
+def model_sizes(rdensity, arch="ampere"):
+    a, b = ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().csrk_model_sizes(float(rdensity), {"volta": 0, "ampere": 1}.get(arch, arch),
+                                  ctypes.byref(a), ctypes.byref(b)), "csrk_model_sizes")
+    return a.value, b.value
+
+
+def tuned_config(h):
+    v = [ctypes.c_int32() for _ in range(5)]
+    _check(lib().csrk_tuned_config(h, *[ctypes.byref(t) for t in v]), "csrk_tuned_config")
+    return dict(zip(("kernel", "lanes", "warps", "stages", "ctas"), (t.value for t in v)))
+
+
+def set_config(h, kernel=-1, lanes=-1, warps=-1, stages=-1, ctas=-1):
+    _check(lib().csrk_set_config(h, kernel, lanes, warps, stages, ctas), "csrk_set_config")
+
+
+def device_status(h, stream=None):
+    st = ctypes.c_int32()
+    rc = lib().csrk_device_status(h, _stream(stream), ctypes.byref(st))
+    if rc not in (0, 7):
+        _check(rc, "csrk_device_status")
+    return st.value
+
+
+def build_info() -> str:
+    return lib().csrk_build_info().decode()
+
+
+class Matrix:
+    """Owning wrapper: ``Matrix(csr, dtype)``; frees the handle when collected."""
+
+    def __init__(self, n, rowptr, colidx, vals, dtype="f64"):
+        self.h = create(n, rowptr, colidx, vals, dtype)
+
+    def __del__(self):
+        h, self.h = getattr(self, "h", None), None
+        if h and _LIB is not None:
+            _LIB.csrk_destroy(h)
+
+    def close(self):
+        destroy(self.h)
+        self.h = None

@@ -1,0 +1,293 @@
+"""GPU parity: the CUDA CSR-k path (through the C ABI) against the FP64 oracle.
+
+Error measure per entry i: |y_gpu - y_ref| / s_i with s_i = |alpha| sum_j |a_ij x_j| +
+|beta| |y_i| (rows with s_i = 0 must match exactly).  Bounds:
+  FP64 values, FP64 accumulation: 1e-12 (the target of the method's FP64 parity).
+  narrowed values (FP32 / BF16) with FP64 accumulation: 1e-12 against the oracle run on the
+    same narrowed values (storage rounding is reproduced bit for bit on the host, so only
+    the accumulation differs).
+  FP32 accumulation with FP32 x: (m_i + 3) * 2^-24 against the oracle on the narrowed
+    values and the FP32-rounded x, m_i the row length (one rounding per add, one for the
+    products, one each for alpha and beta).
+Integer-valued inputs are compared bit for bit.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import precision, spmv as ospmv
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2203_05096_gb300 import csrk  # noqa: E402
+
+DEV = "cuda:0"
+
+
+def make(a, sr=32, ssr=8, dtype="f64", method="rcm", cfg=None, pointers=None):
+    h = csrk.create(a.n, a.rowptr, a.colidx, a.vals, dtype)
+    csrk.reorder(h, method)
+    if pointers is not None:
+        csrk.set_pointers(h, *pointers)
+    else:
+        csrk.set_sizes(h, sr, ssr)
+    if cfg:
+        csrk.set_config(h, **cfg)
+    return h
+
+
+def narrowed(a, dtype):
+    if dtype == "f64":
+        return a.vals
+    if dtype == "f32":
+        return precision.to_f32(a.vals).astype(np.float64)
+    return precision.bf16_bits_to_f64(precision.to_bf16_bits(a.vals))
+
+
+def gpu_spmv(h, x, alpha=1.0, beta=0.0, y0=None, x_f32=False, acc_f32=False, flags=0):
+    dt = torch.float32 if x_f32 else torch.float64
+    xt = torch.tensor(x, dtype=dt, device=DEV)
+    if y0 is None:
+        yt = torch.full((x.shape[0],), float("nan"), dtype=dt, device=DEV)
+    else:
+        yt = torch.tensor(y0, dtype=dt, device=DEV)
+    f = flags | (csrk.X_F32 if x_f32 else 0) | (csrk.ACC_F32 if acc_f32 else 0)
+    csrk.spmv(h, alpha, xt, beta, yt, f)
+    torch.cuda.synchronize()
+    assert csrk.device_status(h) == 0
+    return yt.double().cpu().numpy()
+
+
+def assert_close(got, a, vals, x, alpha=1.0, beta=0.0, y0=None, bound=1e-12, per_row=None):
+    ref = ospmv.csr_spmv(a.n, a.rowptr, a.colidx, vals, x, alpha, beta, y0)
+    s = ospmv.abs_row_scale(a.rowptr, a.colidx, vals, x, alpha, beta, y0)
+    err = np.abs(got - ref)
+    tol = bound * s if per_row is None else per_row * s
+    bad = ~(err <= tol)
+    assert not bad.any(), f"{bad.sum()} rows out of bound; worst {np.max(err / np.where(s > 0, s, 1))}"
+
+
+def small_27pt(seed=3):
+    # 20 x 17 x 15 = 5100 rows: several SSR tiles and a ragged tail for sr=32, ssr=8
+    return synth.stencil_3d(20, 17, 15, 27, "random_dd", seed, labels=synth.vectors.permutation(5100, seed))
+
+
+# ------------------------------------------------------------------ configs[0]
+def test_laplacian_5pt_64x64_fp64():
+    """2-D 5-point Laplacian 64x64, rows randomly permuted (seed 1) then RCM, CSR-3 with
+    SR = 32 rows and SSR = 8 SRs, x ~ U[-1,1] (seed 2), y = Ax."""
+    a = synth.stencil_2d_5pt(64, 64, labels=synth.vectors.permutation(4096, 1))
+    h = make(a, 32, 8)
+    x = synth.uniform_vector(a.n, 2)
+    got = gpu_spmv(h, x)
+    assert_close(got, a, a.vals, x)
+    ones = gpu_spmv(h, np.ones(a.n))
+    assert np.array_equal(ones, ospmv.csr_spmv(a.n, a.rowptr, a.colidx, a.vals, np.ones(a.n)))
+    csrk.destroy(h)
+
+
+CONFIGS = ([dict(kernel=0, lanes=l, warps=w) for l in (1, 2, 4, 8, 32) for w in (1, 4, 8, 16)] +
+           [dict(kernel=0, lanes=1, warps=8, stages=2), dict(kernel=0, lanes=1, warps=8, ctas=2),
+            dict(kernel=0, lanes=4, warps=3, stages=3)] +
+           [dict(kernel=1, lanes=l, warps=w) for l in (1, 4, 32) for w in (1, 8)])
+
+
+@pytest.mark.parametrize("cfg", CONFIGS, ids=lambda c: "-".join(f"{k}{v}" for k, v in c.items()))
+def test_kernel_configs_fp64(cfg):
+    a = small_27pt()
+    h = make(a, 32, 8, cfg=cfg)
+    x = synth.uniform_vector(a.n, 7)
+    assert_close(gpu_spmv(h, x), a, a.vals, x)
+    csrk.destroy(h)
+
+
+@pytest.mark.parametrize("sr,ssr", [(1, 1), (7, 3), (32, 8), (64, 2), (100, 1), (5, 40), (32, 64)])
+def test_size_sweep_ragged(sr, ssr):
+    a = synth.stencil_3d(13, 11, 7, 7, "random_dd", 5, labels=synth.vectors.permutation(1001, 5))
+    x = synth.uniform_vector(a.n, 8)
+    for kernel in (0, 1):
+        h = make(a, sr, ssr, cfg=dict(kernel=kernel))
+        assert_close(gpu_spmv(h, x), a, a.vals, x)
+        csrk.destroy(h)
+
+
+def test_integer_values_bit_exact():
+    a = synth.random_pattern(700, 0.02, 9, integer_values=True, empty_rows=40)
+    x = np.random.default_rng(10).integers(-50, 51, size=a.n).astype(np.float64)
+    ref = ospmv.csr_spmv(a.n, a.rowptr, a.colidx, a.vals, x)
+    for cfg in (dict(kernel=0, lanes=1), dict(kernel=0, lanes=8), dict(kernel=1, lanes=4)):
+        h = make(a, 16, 4, cfg=cfg)
+        assert np.array_equal(gpu_spmv(h, x), ref)
+        csrk.destroy(h)
+
+
+def test_alpha_beta_and_write_only_y():
+    a = small_27pt(4)
+    x = synth.uniform_vector(a.n, 11)
+    y0 = synth.uniform_vector(a.n, 12)
+    h = make(a)
+    assert_close(gpu_spmv(h, x, 2.5, -0.75, y0), a, a.vals, x, 2.5, -0.75, y0)
+    got = gpu_spmv(h, x, -1.0, 0.0, None)            # y starts as NaN, beta == 0
+    assert np.all(np.isfinite(got))
+    assert_close(got, a, a.vals, x, -1.0)
+    csrk.destroy(h)
+
+
+def test_empty_rows_tiny_and_empty_matrix():
+    for a in (synth.random_pattern(50, 0.05, 13, empty_rows=20),
+              synth.random_pattern(1, 1.0, 14), synth.random_pattern(3, 0.0, 15)):
+        x = synth.uniform_vector(a.n, 16)
+        for kernel in (0, 1):
+            h = make(a, 4, 2, cfg=dict(kernel=kernel))
+            assert_close(gpu_spmv(h, x), a, a.vals, x)
+            csrk.destroy(h)
+    h = csrk.create(0, np.zeros(1, np.int32), np.zeros(0, np.int32), np.zeros(0))
+    csrk.set_sizes(h, 32, 8)
+    e = torch.empty(0, dtype=torch.float64, device=DEV)
+    csrk.spmv(h, 1.0, e, 0.0, torch.empty(0, dtype=torch.float64, device=DEV))
+    csrk.destroy(h)
+
+
+def test_fig1_explicit_pointers():
+    a = synth.random_pattern(9, 0.4, 12)
+    x = synth.uniform_vector(9, 13)
+    h = make(a, pointers=([0, 2, 5, 7, 9], [0, 2, 4]), method="none")
+    got = gpu_spmv(h, x)
+    ref3 = ospmv.csr3_spmv(np.array([0, 2, 4]), np.array([0, 2, 5, 7, 9]), a.rowptr, a.colidx, a.vals, x)
+    assert np.allclose(got, ref3, rtol=0, atol=1e-14)
+    assert_close(got, a, a.vals, x)
+    csrk.destroy(h)
+
+
+def test_variable_pointers_random():
+    a = small_27pt(6)
+    rng = np.random.default_rng(6)
+    cuts = np.sort(rng.choice(np.arange(1, a.n), size=120, replace=False))
+    sr_ptr = np.concatenate([[0], cuts, [a.n]])
+    nsr = sr_ptr.size - 1
+    scuts = np.sort(rng.choice(np.arange(1, nsr), size=60, replace=False))
+    ssr_ptr = np.concatenate([[0], scuts, [nsr]])
+    x = synth.uniform_vector(a.n, 17)
+    for kernel in (0, 1):
+        h = make(a, pointers=(sr_ptr, ssr_ptr), cfg=dict(kernel=kernel))
+        assert_close(gpu_spmv(h, x), a, a.vals, x)
+        csrk.destroy(h)
+
+
+# ------------------------------------------------------------------ precision variants
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+@pytest.mark.parametrize("mode", ["x64acc64", "x32acc64", "x32acc32"])
+def test_narrow_values(dtype, mode):
+    a = small_27pt(8)
+    x = synth.uniform_vector(a.n, 18)
+    v = narrowed(a, dtype)
+    x_f32 = mode.startswith("x32")
+    acc_f32 = mode.endswith("acc32")
+    xr = x.astype(np.float32).astype(np.float64) if x_f32 else x
+    for lanes in (1, 4):
+        h = make(a, 32, 8, dtype=dtype, cfg=dict(lanes=lanes))
+        got = gpu_spmv(h, x, x_f32=x_f32, acc_f32=acc_f32)
+        if acc_f32:
+            m = np.diff(a.rowptr.astype(np.int64)).astype(np.float64)
+            assert_close(got, a, v, xr, per_row=(m + 3) * 2.0 ** -24)
+        elif x_f32:
+            # y is stored as FP32: one final rounding on top of the FP64 sum
+            assert_close(got, a, v, xr, per_row=np.full(a.n, 2.0 ** -24 + 1e-12))
+        else:
+            assert_close(got, a, v, xr)
+        csrk.destroy(h)
+
+
+def test_error_vs_fp64_stated():
+    """Per-entry error of the narrowed formats against the FP64 oracle on FP64 values:
+    FP32 within 2^-24 + 1e-12, BF16 within 2^-9 + 1e-12 (relative to s_i)."""
+    a = small_27pt(9)
+    x = synth.uniform_vector(a.n, 19)
+    for dtype, bound in (("f32", 2.0 ** -24), ("bf16", 2.0 ** -9)):
+        h = make(a, dtype=dtype)
+        assert_close(gpu_spmv(h, x), a, a.vals, x, bound=bound + 1e-12)
+        csrk.destroy(h)
+
+
+# ------------------------------------------------------------------ SpMM
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5, 8, 16, 17, 32, 33, 64])
+def test_spmm(k):
+    a = small_27pt(10)
+    X = synth.uniform_block(a.n, k, 20)
+    Y0 = synth.uniform_block(a.n, k, 21)
+    ldx, ldy = k + (k % 3), k + 1
+    Xp = np.zeros((a.n, ldx)); Xp[:, :k] = X
+    Yp = np.zeros((a.n, ldy)); Yp[:, :k] = Y0
+    ref = ospmv.csr_spmm(a.n, a.rowptr, a.colidx, a.vals, X, 1.5, 0.5, Y0)
+    for kernel in (0, 1):
+        h = make(a, 32, 4, cfg=dict(kernel=kernel))
+        Xt = torch.tensor(Xp, device=DEV)
+        Yt = torch.tensor(Yp, device=DEV)
+        csrk.spmm(h, k, 1.5, Xt, ldx, 0.5, Yt, ldy)
+        torch.cuda.synchronize()
+        got = Yt.cpu().numpy()
+        for c in range(k):
+            s = ospmv.abs_row_scale(a.rowptr, a.colidx, a.vals, X[:, c], 1.5, 0.5, Y0[:, c])
+            assert np.all(np.abs(got[:, c] - ref[:, c]) <= 1e-12 * s)
+        assert np.array_equal(got[:, k:], Yp[:, k:])      # padding columns untouched
+        csrk.destroy(h)
+
+
+# ------------------------------------------------------------------ numbering / host vectors
+def test_vec_permuted_and_permute_entry_point():
+    a = small_27pt(11)
+    x = synth.uniform_vector(a.n, 22)
+    h = make(a)
+    perm = csrk.export(h)["perm"]
+    y_nat = gpu_spmv(h, x)
+    xt = torch.tensor(x, device=DEV)
+    xp = torch.empty_like(xt)
+    csrk.permute(h, 0, 1, xt, 1, xp, 1)
+    torch.cuda.synchronize()
+    assert np.array_equal(xp.cpu().numpy(), x[perm])
+    yp = torch.empty_like(xt)
+    csrk.spmv(h, 1.0, xp, 0.0, yp, csrk.VEC_PERMUTED)
+    y2 = torch.empty_like(xt)
+    csrk.permute(h, 1, 1, yp, 1, y2, 1)
+    torch.cuda.synchronize()
+    assert np.array_equal(y2.cpu().numpy(), y_nat)
+    csrk.destroy(h)
+
+
+def test_host_vectors():
+    a = small_27pt(12)
+    x = synth.uniform_vector(a.n, 23)
+    y0 = synth.uniform_vector(a.n, 24)
+    h = make(a)
+    y = y0.copy()
+    csrk.spmv(h, 0.5, x, 2.0, y, csrk.HOST_VECTORS, stream=0)
+    assert_close(y, a, a.vals, x, 0.5, 2.0, y0)
+    csrk.destroy(h)
+
+
+# ------------------------------------------------------------------ full size
+def _full_stencil(points):
+    n = 128 ** 3
+    return synth.stencil_3d(128, 128, 128, points, "random_dd", 3, labels=synth.vectors.permutation(n, 3))
+
+
+@pytest.mark.parametrize("points", [7, 27])
+def test_full_size_128cubed(points):
+    """128^3 stencils at the benchmark's launch configuration: sampled rows against the
+    oracle, plus the Laplacian closed form on every row."""
+    a = _full_stencil(points)
+    h = make(a, 32, 8)
+    x = synth.uniform_vector(a.n, 2)
+    got = gpu_spmv(h, x)
+    rng = np.random.default_rng(0)
+    rows = np.unique(np.concatenate([rng.integers(0, a.n, 20000), np.arange(300), np.arange(a.n - 300, a.n)]))
+    ref = ospmv.csr_spmv_rows(a.rowptr, a.colidx, a.vals, x, rows)
+    s = ospmv.abs_row_scale(a.rowptr, a.colidx, a.vals, x, rows=rows)
+    assert np.all(np.abs(got[rows] - ref) <= 1e-12 * s)
+    csrk.destroy(h)
+    lap = synth.stencil_3d(128, 128, 128, points, "laplacian", labels=synth.vectors.permutation(a.n, 3))
+    h = make(lap, 32, 8)
+    ones = gpu_spmv(h, np.ones(lap.n))
+    assert np.array_equal(ones, ospmv.csr_spmv(lap.n, lap.rowptr, lap.colidx, lap.vals, np.ones(lap.n)))
+    csrk.destroy(h)

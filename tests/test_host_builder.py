@@ -1,0 +1,109 @@
+"""The library's host-side CSR-k builder is bit-exact with the oracle: RCM permutation,
+B = P A P^T, super-row pointers, value narrowing, and the tuning model."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import csrk as ocsrk
+from oracle import precision, reorder, tuning
+from paper_2203_05096_gb300 import csrk
+from tests.conftest import read_golden
+
+
+def build(a, sr=32, ssr=8, method="rcm", dtype="f64"):
+    h = csrk.create(a.n, a.rowptr, a.colidx, a.vals, dtype)
+    perm = csrk.reorder(h, method)
+    csrk.set_sizes(h, sr, ssr)
+    return h, perm
+
+
+def check_against_oracle(a, sr=32, ssr=8):
+    h, perm = build(a, sr, ssr)
+    e = csrk.export(h)
+    ref_perm = reorder.rcm(a.n, a.rowptr, a.colidx)
+    assert np.array_equal(perm, ref_perm)
+    assert np.array_equal(e["perm"], ref_perm)
+    rp, ci, v = reorder.permute_scipy(a.n, a.rowptr, a.colidx, a.vals, ref_perm)
+    assert np.array_equal(e["rowptr"], rp)
+    assert np.array_equal(e["colidx"], ci)
+    assert np.array_equal(e["vals"].view(np.uint64), v.view(np.uint64))
+    srp, ssrp = ocsrk.fixed_pointers(a.n, sr, ssr)
+    assert np.array_equal(e["sr_ptr"], srp) and np.array_equal(e["ssr_ptr"], ssrp)
+    csrk.destroy(h)
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_random_patterns(seed):
+    a = synth.random_pattern(90, 0.03 + 0.01 * seed, seed, symmetric=seed % 2 == 0, empty_rows=seed)
+    check_against_oracle(a, sr=1 + seed, ssr=1 + seed % 3)
+
+
+def test_scrambled_grids_and_fem():
+    check_against_oracle(synth.stencil_2d_5pt(64, 64, labels=synth.vectors.permutation(4096, 1)))
+    check_against_oracle(synth.stencil_3d(20, 17, 15, 27, "random_dd", 3,
+                                          labels=synth.vectors.permutation(5100, 3)), sr=16, ssr=4)
+    check_against_oracle(synth.fem_like(14, 4), sr=32, ssr=4)
+
+
+def test_hand_worked_rcm():
+    from tests.test_oracle_reorder import csr_from_edges, golden_cases
+    for name, n, perm, edges in golden_cases():
+        a = csr_from_edges(n, edges)
+        h, p = build(a, 2, 2)
+        assert p.tolist() == perm, name
+        csrk.destroy(h)
+
+
+@pytest.mark.slow
+def test_full_size_7pt_128_rcm_bit_exact():
+    n = 128 ** 3
+    a = synth.stencil_3d(128, 128, 128, 7, "random_dd", 3, labels=synth.vectors.permutation(n, 3))
+    check_against_oracle(a, 32, 8)
+
+
+def test_second_reorder_composes():
+    a = synth.stencil_2d_5pt(10, 10, labels=synth.vectors.permutation(100, 2))
+    h = csrk.create(a.n, a.rowptr, a.colidx, a.vals)
+    p1 = csrk.reorder(h)
+    p2 = csrk.reorder(h)
+    e = csrk.export(h, with_pointers=False)
+    rp, ci, v = reorder.permute_scipy(a.n, a.rowptr, a.colidx, a.vals, p2)
+    assert np.array_equal(e["colidx"], ci) and np.array_equal(e["vals"], v)
+    csrk.destroy(h)
+
+
+def test_explicit_pointers_fig1():
+    a = synth.random_pattern(9, 0.4, 12)
+    h = csrk.create(a.n, a.rowptr, a.colidx, a.vals)
+    csrk.set_pointers(h, [0, 2, 5, 7, 9], [0, 2, 4])
+    e = csrk.export(h)
+    assert e["sr_ptr"].tolist() == [0, 2, 5, 7, 9] and e["ssr_ptr"].tolist() == [0, 2, 4]
+    assert csrk.info(h)["nssr"] == 2
+    csrk.destroy(h)
+
+
+def test_narrowing_bit_exact():
+    rng = np.random.default_rng(5)
+    cases = []
+    for expr, _bits, _why in read_golden("bf16_cases.txt"):
+        cases.append(eval(expr, {"float": float}))
+    vals = np.concatenate([np.array(cases), rng.standard_normal(3000), rng.standard_normal(500) * 1e-39,
+                           rng.standard_normal(500) * 1e38, rng.uniform(-1, 0, 1000)])
+    n = vals.size
+    rowptr = np.arange(n + 1, dtype=np.int32)
+    colidx = np.zeros(n, np.int32)
+    h = csrk.create(n, rowptr, np.arange(n, dtype=np.int32) * 0 + np.arange(n, dtype=np.int32) % n, vals)
+    got16 = csrk.export_values(h, "bf16")
+    assert np.array_equal(got16, precision.to_bf16_bits(vals))
+    got32 = csrk.export_values(h, "f32")
+    ref32 = precision.to_f32(vals)
+    same = (got32.view(np.uint32) == ref32.view(np.uint32)) | (np.isnan(got32) & np.isnan(ref32))
+    assert np.all(same)
+    csrk.destroy(h)
+
+
+def test_model_sizes_hand_worked():
+    for head, expect, _ in read_golden("tuning_model.txt"):
+        arch, r = head.split()
+        assert csrk.model_sizes(float(r), arch) == tuple(int(v) for v in expect.split()), head
+        assert csrk.model_sizes(float(r), arch) == tuning.model_sizes(float(r), arch)
