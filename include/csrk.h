@@ -187,19 +187,25 @@ int csrk_export_values(csrk_handle h, csrk_dtype dtype, void* out);
  * The library uses it only to seed its autotuner. */
 int csrk_model_sizes(double rdensity, int arch, int32_t* ssrs, int32_t* srs);
 
-/* csrk_tuned_config: the launch configuration the handle will use:
+/* csrk_tuned_config: the launch configuration the handle will use (any pointer may be
+ * NULL):
  *   kernel   0 = TMA-staged super-super-row kernel, 1 = direct-load kernel
- *   lanes    lanes cooperating on one row (SpMV)
- *   warps    consumer warps per thread block
- *   stages   shared-memory pipeline depth (TMA kernel)
- *   ctas     thread blocks per SM */
-int csrk_tuned_config(csrk_handle h, int32_t* kernel, int32_t* lanes, int32_t* warps,
-                      int32_t* stages, int32_t* ctas);
+ *   lanes    lanes cooperating on one row (SpMV): 1, 2, 4, 8 or 32
+ *   unroll   x gathers a lane issues before consuming them; compiled (lanes, unroll)
+ *            pairs: (1,4) (1,8) (1,16) (1,32) (2,8) (2,16) (4,8) (8,8) (32,4)
+ *   warps    consumer warps per thread block (1..16)
+ *   stages   shared-memory pipeline depth of the TMA kernel (0 = as many as fit)
+ *   ctas     thread blocks per SM (TMA kernel) */
+int csrk_tuned_config(csrk_handle h, int32_t* kernel, int32_t* lanes, int32_t* unroll,
+                      int32_t* warps, int32_t* stages, int32_t* ctas);
 
-/* csrk_set_config: force a launch configuration (same fields as csrk_tuned_config;
- * a negative field keeps the current value).  Used by the autotuner and tests. */
-int csrk_set_config(csrk_handle h, int32_t kernel, int32_t lanes, int32_t warps,
-                    int32_t stages, int32_t ctas);
+/* csrk_set_config: force a launch configuration (same fields as csrk_tuned_config; a
+ * negative field keeps the current value; a new lanes value without an unroll picks the
+ * default unroll for it).  A forced TMA kernel whose super-super-rows do not fit two
+ * shared-memory stages makes the compute calls return CSRK_ERR_UNSUPPORTED.  Used by the
+ * autotuner and tests. */
+int csrk_set_config(csrk_handle h, int32_t kernel, int32_t lanes, int32_t unroll,
+                    int32_t warps, int32_t stages, int32_t ctas);
 
 /* csrk_device_status: synchronise the handle's work on `stream` and return the device
  * status word (0 = clean; bit 0 = a pipeline wait ran out) in *status, then clear it.

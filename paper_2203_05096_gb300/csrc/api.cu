@@ -54,7 +54,8 @@ struct csrk_matrix {
     int device = -1;
     int num_sms = 0;
     int smem_per_sm = 0, smem_optin = 0;
-    bool dev_struct = false;       // rowptr/colidx/pointers/desc/perm uploaded
+    bool dev_struct = false;       // rowptr/colidx/perm uploaded
+    bool dev_ptrs = false;         // sr_ptr/desc uploaded
     int32_t* d_rowptr = nullptr;
     int32_t* d_colidx = nullptr;
     void* d_vals[3] = {nullptr, nullptr, nullptr};
@@ -69,14 +70,20 @@ struct csrk_matrix {
 
 namespace {
 
-void free_struct(csrk_matrix* h) {
-    cudaFree(h->d_rowptr);
-    cudaFree(h->d_colidx);
+void free_ptrs(csrk_matrix* h) {
     cudaFree(h->d_sr_ptr);
     cudaFree(h->d_desc);
-    cudaFree(h->d_perm);
-    h->d_rowptr = h->d_colidx = h->d_sr_ptr = h->d_perm = nullptr;
+    h->d_sr_ptr = nullptr;
     h->d_desc = nullptr;
+    h->dev_ptrs = false;
+}
+
+void free_struct(csrk_matrix* h) {
+    free_ptrs(h);
+    cudaFree(h->d_rowptr);
+    cudaFree(h->d_colidx);
+    cudaFree(h->d_perm);
+    h->d_rowptr = h->d_colidx = h->d_perm = nullptr;
     h->dev_struct = false;
 }
 
@@ -134,16 +141,20 @@ int ensure_context(csrk_matrix* h) {
 }
 
 int ensure_struct(csrk_matrix* h) {
-    if (h->dev_struct) return CSRK_OK;
     const CsrHost& m = h->m;
     int rc;
-    if ((rc = upload_padded(&h->d_rowptr, m.rowptr.data(), m.rowptr.size(), 4, "rowptr"))) return rc;
-    if ((rc = upload_padded(&h->d_colidx, m.colidx.data(), m.colidx.size(), 4, "colidx"))) return rc;
-    if ((rc = upload_padded(&h->d_sr_ptr, h->sr_ptr.data(), h->sr_ptr.size(), 4, "sr_ptr"))) return rc;
-    if ((rc = upload_padded(&h->d_desc, h->desc.data(), h->desc.size(), sizeof(SsrDesc), "desc"))) return rc;
-    if (!h->perm.empty())
-        if ((rc = upload_padded(&h->d_perm, h->perm.data(), h->perm.size(), 4, "perm"))) return rc;
-    h->dev_struct = true;
+    if (!h->dev_struct) {
+        if ((rc = upload_padded(&h->d_rowptr, m.rowptr.data(), m.rowptr.size(), 4, "rowptr"))) return rc;
+        if ((rc = upload_padded(&h->d_colidx, m.colidx.data(), m.colidx.size(), 4, "colidx"))) return rc;
+        if (!h->perm.empty())
+            if ((rc = upload_padded(&h->d_perm, h->perm.data(), h->perm.size(), 4, "perm"))) return rc;
+        h->dev_struct = true;
+    }
+    if (!h->dev_ptrs) {
+        if ((rc = upload_padded(&h->d_sr_ptr, h->sr_ptr.data(), h->sr_ptr.size(), 4, "sr_ptr"))) return rc;
+        if ((rc = upload_padded(&h->d_desc, h->desc.data(), h->desc.size(), sizeof(SsrDesc), "desc"))) return rc;
+        h->dev_ptrs = true;
+    }
     return CSRK_OK;
 }
 
@@ -182,6 +193,32 @@ int default_lanes(const csrk_matrix* h) {
     if (mean <= 128) return 4;
     if (mean <= 256) return 8;
     return 32;
+}
+
+// (lanes, unroll) pairs compiled into the kernels.
+bool pair_compiled(int lanes, int unroll) {
+    static const int pairs[][2] = {{1, 4}, {1, 8}, {1, 16}, {1, 32}, {2, 8}, {2, 16}, {4, 8}, {8, 8}, {32, 4}};
+    for (auto& p : pairs)
+        if (p[0] == lanes && p[1] == unroll) return true;
+    return false;
+}
+
+// Gather chunk for a lane count: the smallest compiled chunk that covers a lane's share of
+// the longest row (so a whole row's x gathers are in flight at once), capped at 32.
+int default_unroll(int lanes, int max_row_len) {
+    const int share = (max_row_len + lanes - 1) / std::max(1, lanes);
+    for (int u : {4, 8, 16, 32})
+        if (share <= u && pair_compiled(lanes, u)) return u;
+    for (int u : {32, 16, 8, 4})
+        if (pair_compiled(lanes, u)) return u;
+    return 4;
+}
+
+KernelConfig default_config(const csrk_matrix* h) {
+    KernelConfig c;
+    c.lanes = default_lanes(h);
+    c.unroll = default_unroll(c.lanes, h->have_ptrs ? h->stats.max_row_len : 32);
+    return c;
 }
 
 int smem_budget(const csrk_matrix* h, int ctas) {
@@ -228,11 +265,7 @@ namespace {
 
 // Resolve the launch configuration and stage plan for this handle and value type.
 int resolve_config(csrk_matrix* h, int vt, KernelConfig& cfg, StagePlan& plan) {
-    cfg = h->cfg;
-    if (!h->cfg_set) {
-        cfg = KernelConfig{};
-        cfg.lanes = default_lanes(h);
-    }
+    cfg = h->cfg_set ? h->cfg : default_config(h);
     plan = StagePlan{};
     if (cfg.kernel == 0) {
         if (!plan_stages(h->stats, (int)val_size(vt), smem_budget(h, cfg.ctas), cfg.stages, plan)) {
@@ -242,8 +275,6 @@ int resolve_config(csrk_matrix* h, int vt, KernelConfig& cfg, StagePlan& plan) {
             cfg.kernel = 1;   // the SSRs do not fit: fall back to direct loads
         }
     }
-    if (cfg.kernel == 1 && cfg.lanes != 1 && cfg.lanes != 4 && cfg.lanes != 32)
-        cfg.lanes = cfg.lanes < 4 ? 1 : (cfg.lanes < 32 ? 4 : 32);
     return CSRK_OK;
 }
 
@@ -407,7 +438,7 @@ static int install_pointers(csrk_handle h, std::vector<int32_t>&& srp, std::vect
     h->ssr_ptr = std::move(ssrp);
     build_descs(h->m, h->sr_ptr, h->ssr_ptr, h->desc, h->stats);
     h->have_ptrs = true;
-    if (h->dev_struct) free_struct(h);   // pointer arrays changed: re-upload on next use
+    if (h->dev_ptrs) free_ptrs(h);   // pointer arrays changed: re-upload on next use
     return CSRK_OK;
 }
 
@@ -562,30 +593,23 @@ int csrk_model_sizes(double rdensity, int arch, int32_t* ssrs, int32_t* srs) {
     return CSRK_OK;
 }
 
-int csrk_tuned_config(csrk_handle h, int32_t* kernel, int32_t* lanes, int32_t* warps,
-                      int32_t* stages, int32_t* ctas) {
+int csrk_tuned_config(csrk_handle h, int32_t* kernel, int32_t* lanes, int32_t* unroll,
+                      int32_t* warps, int32_t* stages, int32_t* ctas) {
     if (!h) return fail(CSRK_ERR_ARG, "handle is NULL");
-    KernelConfig c = h->cfg;
-    if (!h->cfg_set) {
-        c = KernelConfig{};
-        c.lanes = default_lanes(h);
-    }
+    KernelConfig c = h->cfg_set ? h->cfg : default_config(h);
     if (kernel) *kernel = c.kernel;
     if (lanes) *lanes = c.lanes;
+    if (unroll) *unroll = c.unroll;
     if (warps) *warps = c.warps;
     if (stages) *stages = c.stages;
     if (ctas) *ctas = c.ctas;
     return CSRK_OK;
 }
 
-int csrk_set_config(csrk_handle h, int32_t kernel, int32_t lanes, int32_t warps, int32_t stages,
-                    int32_t ctas) {
+int csrk_set_config(csrk_handle h, int32_t kernel, int32_t lanes, int32_t unroll, int32_t warps,
+                    int32_t stages, int32_t ctas) {
     if (!h) return fail(CSRK_ERR_ARG, "handle is NULL");
-    KernelConfig c = h->cfg;
-    if (!h->cfg_set) {
-        c = KernelConfig{};
-        c.lanes = default_lanes(h);
-    }
+    KernelConfig c = h->cfg_set ? h->cfg : default_config(h);
     if (kernel >= 0) {
         if (kernel > 1) return fail(CSRK_ERR_ARG, "kernel must be 0 or 1");
         c.kernel = kernel;
@@ -594,7 +618,12 @@ int csrk_set_config(csrk_handle h, int32_t kernel, int32_t lanes, int32_t warps,
         if (lanes != 1 && lanes != 2 && lanes != 4 && lanes != 8 && lanes != 32)
             return fail(CSRK_ERR_ARG, "lanes must be 1, 2, 4, 8 or 32");
         c.lanes = lanes;
+        if (unroll < 0) c.unroll = default_unroll(lanes, h->have_ptrs ? h->stats.max_row_len : 32);
     }
+    if (unroll >= 0) c.unroll = unroll;
+    if (!pair_compiled(c.lanes, c.unroll))
+        return fail(CSRK_ERR_ARG, "unsupported (lanes, unroll) pair; compiled: (1,4) (1,8) (1,16) "
+                                  "(1,32) (2,8) (2,16) (4,8) (8,8) (32,4)");
     if (warps >= 0) {
         if (warps < 1 || warps > 16) return fail(CSRK_ERR_ARG, "warps must be in [1, 16]");
         c.warps = warps;

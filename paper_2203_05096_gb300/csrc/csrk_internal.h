@@ -63,6 +63,7 @@ enum ValType { VAL_F64 = 0, VAL_F32 = 1, VAL_BF16 = 2 };
 struct KernelConfig {
     int kernel = 0;    // 0 TMA-staged, 1 direct loads
     int lanes = 1;     // lanes per row (SpMV)
+    int unroll = 8;    // x gathers issued per lane before the FMAs consume them
     int warps = 8;     // consumer warps per CTA
     int stages = 0;    // 0 = as many as fit
     int ctas = 1;      // CTAs per SM

@@ -172,8 +172,11 @@ __device__ __forceinline__ void store_y(XT* y, int64_t idx, AT acc, double alpha
 
 // ------------------------------------------------------------------ row compute
 // One pass of a warp over up to 32/LPR rows [rb + lane/LPR ...] of a super-row.
-// col_s / val_s are indexable by absolute nonzero index (already offset).
-template <typename VT, typename XT, typename AT, int LPR>
+// col_s / val_s are indexable by absolute nonzero index (already offset).  Each lane walks
+// its row's nonzeros sub, sub+LPR, ... in chunks of U: it first issues the U independent
+// x gathers of the chunk (the long-latency loads, all in flight together), then runs the
+// chunk's U FMAs in stored order.
+template <typename VT, typename XT, typename AT, int LPR, int U>
 __device__ __forceinline__ void spmv_rows(int rb, int re, const int32_t* __restrict__ rp,
                                           const int32_t* __restrict__ col_s,
                                           const VT* __restrict__ val_s,
@@ -185,10 +188,20 @@ __device__ __forceinline__ void spmv_rows(int rb, int re, const int32_t* __restr
         const int r = base + lane / LPR;
         AT acc = 0;
         if (r < re) {
-            const int pb = rp[r], pe = rp[r + 1];
-            int p = pb + sub;
-#pragma unroll 4
-            for (; p < pe; p += LPR) acc = Acc<AT>::fma(val_s[p], ldg_x(&x[col_s[p]]), acc);
+            const int pe = rp[r + 1];
+            for (int c = rp[r] + sub; c < pe; c += U * LPR) {
+                XT xv[U];
+#pragma unroll
+                for (int t = 0; t < U; ++t) {
+                    const int p = c + t * LPR;
+                    if (p < pe) xv[t] = ldg_x(&x[col_s[p]]);
+                }
+#pragma unroll
+                for (int t = 0; t < U; ++t) {
+                    const int p = c + t * LPR;
+                    if (p < pe) acc = Acc<AT>::fma(val_s[p], xv[t], acc);
+                }
+            }
         }
         if constexpr (LPR > 1) {
 #pragma unroll
@@ -263,9 +276,9 @@ __device__ __forceinline__ void slice16(int64_t first, int64_t last_excl, int64_
     bytes = (uint32_t)((a1 - a0) * ESZ);
 }
 
-// MODE 0: SpMV with LPR lanes per row.  MODE 1: SpMM with G = LPR lanes per row and CPL
-// columns per lane.
-template <typename VT, typename XT, typename AT, int LPR, int MODE, int CPL>
+// MODE 0: SpMV with LPR lanes per row and gather chunks of U.  MODE 1: SpMM with G = LPR
+// lanes per row and U columns per lane.
+template <typename VT, typename XT, typename AT, int LPR, int MODE, int U>
 __global__ void __launch_bounds__(544, 1) csr3_tma_kernel(const TmaParams P) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int S = P.stages;
@@ -345,10 +358,10 @@ __global__ void __launch_bounds__(544, 1) csr3_tma_kernel(const TmaParams P) {
             const int sr = d.s0 + j;
             const int rb = srp[sr], re = srp[sr + 1];
             if constexpr (MODE == 0)
-                spmv_rows<VT, XT, AT, LPR>(rb, re, rp, col, val, x, y, P.alpha, P.beta, lane);
+                spmv_rows<VT, XT, AT, LPR, U>(rb, re, rp, col, val, x, y, P.alpha, P.beta, lane);
             else
-                spmm_rows<VT, XT, AT, LPR, CPL>(rb, re, rp, col, val, x, P.ldx, y, P.ldy, P.k,
-                                                 P.alpha, P.beta, lane);
+                spmm_rows<VT, XT, AT, LPR, U>(rb, re, rp, col, val, x, P.ldx, y, P.ldy, P.k,
+                                               P.alpha, P.beta, lane);
         }
         sr_seq += nsr;
         __syncwarp();
@@ -360,7 +373,7 @@ __global__ void __launch_bounds__(544, 1) csr3_tma_kernel(const TmaParams P) {
 // One block per SSR (the paper's 1-D grid), consumer warps stride the SSR's super-rows,
 // operands read straight from global memory.  Used when an SSR does not fit a stage and
 // as an autotuner alternative.
-template <typename VT, typename XT, typename AT, int LPR, int MODE, int CPL>
+template <typename VT, typename XT, typename AT, int LPR, int MODE, int U>
 __global__ void __launch_bounds__(512, 1) csr3_direct_kernel(const TmaParams P) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int W = blockDim.x >> 5;
@@ -372,11 +385,11 @@ __global__ void __launch_bounds__(512, 1) csr3_direct_kernel(const TmaParams P) 
         for (int sr = d.s0 + warp; sr < d.s1; sr += W) {
             const int rb = __ldg(&P.sr_ptr[sr]), re = __ldg(&P.sr_ptr[sr + 1]);
             if constexpr (MODE == 0)
-                spmv_rows<VT, XT, AT, LPR>(rb, re, P.rowptr, P.colidx, vals, x, y, P.alpha,
-                                           P.beta, lane);
+                spmv_rows<VT, XT, AT, LPR, U>(rb, re, P.rowptr, P.colidx, vals, x, y, P.alpha,
+                                              P.beta, lane);
             else
-                spmm_rows<VT, XT, AT, LPR, CPL>(rb, re, P.rowptr, P.colidx, vals, x, P.ldx, y,
-                                                 P.ldy, P.k, P.alpha, P.beta, lane);
+                spmm_rows<VT, XT, AT, LPR, U>(rb, re, P.rowptr, P.colidx, vals, x, P.ldx, y,
+                                               P.ldy, P.k, P.alpha, P.beta, lane);
         }
     }
 }

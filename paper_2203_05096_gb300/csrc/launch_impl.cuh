@@ -8,7 +8,7 @@
 namespace csrk {
 namespace dev {
 
-template <typename VT, typename XT, typename AT, int LPR, int MODE, int CPL>
+template <typename VT, typename XT, typename AT, int LPR, int MODE, int U>
 static int launch_one(const LaunchArgs& a, const KernelConfig& cfg, const StagePlan& plan,
                       cudaStream_t stream) {
     TmaParams P;
@@ -36,7 +36,7 @@ static int launch_one(const LaunchArgs& a, const KernelConfig& cfg, const StageP
     P.timeout_ns = a.timeout_ns;
     if (a.nssr == 0) return 0;
     if (cfg.kernel == 0) {
-        auto kern = csr3_tma_kernel<VT, XT, AT, LPR, MODE, CPL>;
+        auto kern = csr3_tma_kernel<VT, XT, AT, LPR, MODE, U>;
         const int smem = (int)(plan.header_bytes + (size_t)plan.stages * plan.stage_bytes);
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return (int)e;
@@ -45,7 +45,7 @@ static int launch_one(const LaunchArgs& a, const KernelConfig& cfg, const StageP
         if (grid > a.nssr) grid = a.nssr;
         kern<<<grid, threads, smem, stream>>>(P);
     } else {
-        auto kern = csr3_direct_kernel<VT, XT, AT, LPR, MODE, CPL>;
+        auto kern = csr3_direct_kernel<VT, XT, AT, LPR, MODE, U>;
         const int threads = 32 * cfg.warps;
         int grid = a.nssr;
         kern<<<grid, threads, 0, stream>>>(P);
@@ -53,26 +53,25 @@ static int launch_one(const LaunchArgs& a, const KernelConfig& cfg, const StageP
     return (int)cudaGetLastError();
 }
 
+// SpMV (lanes, unroll) pairs compiled in: row per lane with gather chunks of 4..32, and
+// 2..32 lanes per row for long rows.
+#define CSRK_SPMV_CASE(L, UU) \
+    if (cfg.lanes == L && cfg.unroll == UU) return launch_one<VT, XT, AT, L, 0, UU>(a, cfg, plan, s);
+
 template <typename VT, typename XT, typename AT>
 static int dispatch_lanes(const LaunchArgs& a, const KernelConfig& cfg, const StagePlan& plan,
                           cudaStream_t s) {
     if (!a.spmm) {
-        if (cfg.kernel == 0) {
-            switch (cfg.lanes) {
-                case 1: return launch_one<VT, XT, AT, 1, 0, 1>(a, cfg, plan, s);
-                case 2: return launch_one<VT, XT, AT, 2, 0, 1>(a, cfg, plan, s);
-                case 4: return launch_one<VT, XT, AT, 4, 0, 1>(a, cfg, plan, s);
-                case 8: return launch_one<VT, XT, AT, 8, 0, 1>(a, cfg, plan, s);
-                case 32: return launch_one<VT, XT, AT, 32, 0, 1>(a, cfg, plan, s);
-                default: return -1;
-            }
-        }
-        switch (cfg.lanes) {
-            case 1: return launch_one<VT, XT, AT, 1, 0, 1>(a, cfg, plan, s);
-            case 4: return launch_one<VT, XT, AT, 4, 0, 1>(a, cfg, plan, s);
-            case 32: return launch_one<VT, XT, AT, 32, 0, 1>(a, cfg, plan, s);
-            default: return -1;
-        }
+        CSRK_SPMV_CASE(1, 4)
+        CSRK_SPMV_CASE(1, 8)
+        CSRK_SPMV_CASE(1, 16)
+        CSRK_SPMV_CASE(1, 32)
+        CSRK_SPMV_CASE(2, 8)
+        CSRK_SPMV_CASE(2, 16)
+        CSRK_SPMV_CASE(4, 8)
+        CSRK_SPMV_CASE(8, 8)
+        CSRK_SPMV_CASE(32, 4)
+        return -1;
     }
     // SpMM: G lanes per row, columns split across them, at most 2 per lane.
     const int k = a.k;
@@ -84,6 +83,7 @@ static int dispatch_lanes(const LaunchArgs& a, const KernelConfig& cfg, const St
     if (k <= 64) return launch_one<VT, XT, AT, 32, 1, 2>(a, cfg, plan, s);
     return -1;
 }
+#undef CSRK_SPMV_CASE
 
 }  // namespace dev
 }  // namespace csrk

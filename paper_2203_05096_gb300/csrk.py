@@ -53,8 +53,8 @@ _PROTOS = {
     "csrk_export": [_vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "csrk_export_values": [_vp, ctypes.c_int, _vp],
     "csrk_model_sizes": [_d, ctypes.c_int, _pi32, _pi32],
-    "csrk_tuned_config": [_vp, _pi32, _pi32, _pi32, _pi32, _pi32],
-    "csrk_set_config": [_vp, _i32, _i32, _i32, _i32, _i32],
+    "csrk_tuned_config": [_vp, _pi32, _pi32, _pi32, _pi32, _pi32, _pi32],
+    "csrk_set_config": [_vp, _i32, _i32, _i32, _i32, _i32, _i32],
     "csrk_device_status": [_vp, _vp, _pi32],
 }
 
@@ -205,13 +205,13 @@ def model_sizes(rdensity, arch="ampere"):
 
 
 def tuned_config(h):
-    v = [ctypes.c_int32() for _ in range(5)]
+    v = [ctypes.c_int32() for _ in range(6)]
     _check(lib().csrk_tuned_config(h, *[ctypes.byref(t) for t in v]), "csrk_tuned_config")
-    return dict(zip(("kernel", "lanes", "warps", "stages", "ctas"), (t.value for t in v)))
+    return dict(zip(("kernel", "lanes", "unroll", "warps", "stages", "ctas"), (t.value for t in v)))
 
 
-def set_config(h, kernel=-1, lanes=-1, warps=-1, stages=-1, ctas=-1):
-    _check(lib().csrk_set_config(h, kernel, lanes, warps, stages, ctas), "csrk_set_config")
+def set_config(h, kernel=-1, lanes=-1, unroll=-1, warps=-1, stages=-1, ctas=-1):
+    _check(lib().csrk_set_config(h, kernel, lanes, unroll, warps, stages, ctas), "csrk_set_config")
 
 
 def device_status(h, stream=None):

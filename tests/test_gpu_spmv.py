@@ -87,16 +87,19 @@ def test_laplacian_5pt_64x64_fp64():
     csrk.destroy(h)
 
 
-CONFIGS = ([dict(kernel=0, lanes=l, warps=w) for l in (1, 2, 4, 8, 32) for w in (1, 4, 8, 16)] +
+PAIRS = [(1, 4), (1, 8), (1, 16), (1, 32), (2, 8), (2, 16), (4, 8), (8, 8), (32, 4)]
+CONFIGS = ([dict(kernel=0, lanes=l, unroll=u, warps=w) for l, u in PAIRS for w in (1, 8)] +
+           [dict(kernel=0, lanes=1, unroll=32, warps=w) for w in (4, 16)] +
            [dict(kernel=0, lanes=1, warps=8, stages=2), dict(kernel=0, lanes=1, warps=8, ctas=2),
             dict(kernel=0, lanes=4, warps=3, stages=3)] +
-           [dict(kernel=1, lanes=l, warps=w) for l in (1, 4, 32) for w in (1, 8)])
+           [dict(kernel=1, lanes=l, unroll=u, warps=w) for l, u in PAIRS for w in (1, 8)])
 
 
 @pytest.mark.parametrize("cfg", CONFIGS, ids=lambda c: "-".join(f"{k}{v}" for k, v in c.items()))
 def test_kernel_configs_fp64(cfg):
     a = small_27pt()
-    h = make(a, 32, 8, cfg=cfg)
+    # two blocks per SM halve the shared memory: 256-row 27-point SSRs no longer fit two stages
+    h = make(a, 32, 4 if cfg.get("ctas", 1) > 1 else 8, cfg=cfg)
     x = synth.uniform_vector(a.n, 7)
     assert_close(gpu_spmv(h, x), a, a.vals, x)
     csrk.destroy(h)
@@ -201,10 +204,12 @@ def test_narrow_values(dtype, mode):
 
 def test_error_vs_fp64_stated():
     """Per-entry error of the narrowed formats against the FP64 oracle on FP64 values:
-    FP32 within 2^-24 + 1e-12, BF16 within 2^-9 + 1e-12 (relative to s_i)."""
+    within the format's unit roundoff u = 2^-p for p significant bits (FP32: 2^-24,
+    BF16: 2^-8) plus 1e-12, relative to s_i: each stored value moves by at most u times
+    itself, so the row sum moves by at most u * s_i."""
     a = small_27pt(9)
     x = synth.uniform_vector(a.n, 19)
-    for dtype, bound in (("f32", 2.0 ** -24), ("bf16", 2.0 ** -9)):
+    for dtype, bound in (("f32", 2.0 ** -24), ("bf16", 2.0 ** -8)):
         h = make(a, dtype=dtype)
         assert_close(gpu_spmv(h, x), a, a.vals, x, bound=bound + 1e-12)
         csrk.destroy(h)
