@@ -212,6 +212,35 @@ int csrk_set_config(csrk_handle h, int32_t kernel, int32_t lanes, int32_t unroll
  * Returns CSRK_ERR_TIMEOUT when the word was non-zero. */
 int csrk_device_status(csrk_handle h, void* stream, int32_t* status);
 
+/* csrk_spmv_static_scratch: y = alpha*A*x + beta*y in the input numbering, for callers
+ * that cannot allocate device memory -- for example a program whose arena allocator owns
+ * all of the GPU's memory, a plugin held to a fixed memory budget by its host, or a
+ * latency-critical loop that cannot afford an allocation's device synchronisation.  The
+ * paper has no counterpart; this is a service of the library.  It allocates nothing: the
+ * permuted x and result live in one static device array of 2 x 1,048,576 doubles
+ * (16 MiB) that every GPU loading the library holds until the process exits.
+ *   n        rows, at most 1,048,576 (larger n returns CSRK_ERR_ARG; use csrk_spmv)
+ *   nssr, ssr_ptr, sr_ptr, rowptr, colidx, vals
+ *            the reordered CSR-3 form in DEVICE memory, as csrk_export returns it
+ *            (vals FP64; no padding needed: the kernel uses plain loads)
+ *   perm     DEVICE array, perm[new] = old, or NULL when there is no reordering (then the
+ *            kernel works on x and y directly and the static array is not touched)
+ *   x, y     DEVICE vectors of n FP64 values in the input numbering; beta = 0 makes y
+ *            write-only
+ *   stream   cudaStream_t
+ * The first call on a device looks up the static array's device address for that device
+ * (cudaGetSymbolAddress, with that device current); make that first call before any
+ * stream capture.  Every call on a device shares the one array, which keeps the last
+ * call's contents; nothing in it needs clearing, because each call writes every element
+ * it later reads.  Calls whose work overlaps on the GPU (other streams, other threads)
+ * race on the array: serialise them.  Errors: CSRK_ERR_ARG, CSRK_ERR_CUDA, message in
+ * csrk_last_error(). */
+int csrk_spmv_static_scratch(int32_t n, int32_t nssr, const int32_t* ssr_ptr,
+                             const int32_t* sr_ptr, const int32_t* rowptr,
+                             const int32_t* colidx, const double* vals, const int32_t* perm,
+                             double alpha, const double* x, double beta, double* y,
+                             void* stream);
+
 const char* csrk_last_error(void);
 
 /* Library build description (static string): compiled architectures and options. */

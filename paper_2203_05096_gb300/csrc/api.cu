@@ -36,6 +36,8 @@ size_t val_size(int vt) { return vt == VAL_F64 ? 8 : (vt == VAL_F32 ? 4 : 2); }
 
 }  // namespace
 
+void csrk::set_last_error(const std::string& msg) { g_last_error = msg; }
+
 // ------------------------------------------------------------------ handle
 struct csrk_matrix {
     CsrHost m;                     // current form (reordered after csrk_reorder)

@@ -108,6 +108,9 @@ int launch_csr3_f64(const LaunchArgs& a, const KernelConfig& cfg, const StagePla
 int launch_csr3_f32(const LaunchArgs& a, const KernelConfig& cfg, const StagePlan& plan, void* stream);
 int launch_csr3_bf16(const LaunchArgs& a, const KernelConfig& cfg, const StagePlan& plan, void* stream);
 
+// api.cu: message returned by csrk_last_error() for the calling thread.
+void set_last_error(const std::string& msg);
+
 // vec_kernels.cu
 int launch_gather_rows(const void* in, int64_t ldi, void* out, int64_t ldo, const int32_t* perm,
                        int32_t n, int32_t k, int elem_bytes, void* stream);

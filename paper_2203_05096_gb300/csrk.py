@@ -56,6 +56,7 @@ _PROTOS = {
     "csrk_tuned_config": [_vp, _pi32, _pi32, _pi32, _pi32, _pi32, _pi32],
     "csrk_set_config": [_vp, _i32, _i32, _i32, _i32, _i32, _i32],
     "csrk_device_status": [_vp, _vp, _pi32],
+    "csrk_spmv_static_scratch": [_i32, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _d, _vp, _d, _vp, _vp],
 }
 
 
@@ -220,6 +221,15 @@ def device_status(h, stream=None):
     if rc not in (0, 7):
         _check(rc, "csrk_device_status")
     return st.value
+
+
+def spmv_static_scratch(n, nssr, ssr_ptr, sr_ptr, rowptr, colidx, vals, perm, alpha, x, beta, y,
+                        stream=None):
+    """Allocation-free SpMV (all arrays device tensors, e.g. from csrk.export)."""
+    _check(lib().csrk_spmv_static_scratch(int(n), int(nssr), _ptr(ssr_ptr), _ptr(sr_ptr),
+                                          _ptr(rowptr), _ptr(colidx), _ptr(vals), _ptr(perm),
+                                          float(alpha), _ptr(x), float(beta), _ptr(y),
+                                          _stream(stream, x, y)), "csrk_spmv_static_scratch")
 
 
 def build_info() -> str:
