@@ -188,14 +188,19 @@ def run_ours(args, world, rank, local):
     for name, a in mats:
         h = csrk.create(a.n, a.rowptr, a.colidx, a.vals, args.dtype)
         csrk.reorder(h, "rcm", want_perm=False)
-        csrk.set_sizes(h, SR, SSR)
+        t_tune = time.perf_counter()
+        if args.sizes == "auto":
+            csrk.set_sizes(h, 0, 0)          # the library's autotuner (timed on this matrix)
+        else:
+            csrk.set_sizes(h, *(int(v) for v in args.sizes.split(",")))
+        t_tune = time.perf_counter() - t_tune
         if args.config:
             csrk.set_config(h, **{k: int(v) for k, v in (kv.split("=") for kv in args.config.split(","))})
         inf = csrk.info(h)
         x = torch.tensor(synth.uniform_vector(a.n, 2), dtype=torch.float64, device=dev)
         xp, yp, y = torch.empty_like(x), torch.empty_like(x), torch.empty_like(x)
         state.append(dict(name=name, a=a, h=h, info=inf, x=x, xp=xp, yp=yp, y=y,
-                          cfg=csrk.tuned_config(h)))
+                          cfg=csrk.tuned_config(h), tune_s=t_tune))
 
     perm_fn, spmv_fn = lib.csrk_permute, lib.csrk_spmv
     VP = csrk.VEC_PERMUTED
@@ -282,7 +287,8 @@ def run_ours(args, world, rank, local):
                                  "kernel_gflops": round(2.0 * inf["nnz"] / (km * 1e-3) / 1e9, 1),
                                  "kernel_gbs": round(b / (km * 1e-3) / 1e9, 1),
                                  "kernel_frac_of_peak": round(b / (km * 1e-3) / 1e9 / peak, 3),
-                                 "config": s["cfg"]}
+                                 "sr": inf["sr"], "ssr": inf["ssr"], "config": s["cfg"],
+                                 "setup_s": round(s["tune_s"], 2)}
 
     # end to end: the public call with host vectors (pinned), copies inside the timed region
     e2e = None
@@ -336,9 +342,10 @@ def run_ours(args, world, rank, local):
             "dtype": args.dtype,
             "data": "synthetic",
             "config": {"workload": "128^3 7-point and 27-point random diagonally dominant stencils, "
-                                   "random symmetric permutation undone by RCM, CSR-3 SR=32 rows, SSR=8 SRs, "
-                                   "y=Ax per matrix per step (permute x, CSR-3 kernel, unpermute y)",
-                       "sr": SR, "ssr": SSR, "l2": "inputs larger than L2 (~930 MB per step vs 129 MB)",
+                                   "random symmetric permutation undone by RCM, CSR-3 sizes and launch "
+                                   "shape from the library autotuner, y=Ax per matrix per step "
+                                   "(permute x, CSR-3 kernel, unpermute y)",
+                       "sizes": args.sizes, "l2": "inputs larger than L2 (~930 MB per step vs 129 MB)",
                        "parallelism": f"replicas x{world}", "per_matrix": per_matrix},
             "roofline": {"bound": "hbm", "kernel": f"csr3 {state[dom]['name']}",
                          "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
@@ -423,6 +430,7 @@ def main():
     p.add_argument("--impl", choices=("ours", "reference"), default="ours")
     p.add_argument("--dtype", choices=("f64", "f32", "bf16"), default="f64")
     p.add_argument("--config", default="", help="force a launch config, e.g. kernel=0,lanes=1,warps=8")
+    p.add_argument("--sizes", default="auto", help="'auto' (autotuner) or 'sr,ssr'")
     p.add_argument("--cpu-seconds", type=float, default=10.0)
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-e2e", action="store_true")

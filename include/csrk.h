@@ -195,15 +195,19 @@ int csrk_model_sizes(double rdensity, int arch, int32_t* ssrs, int32_t* srs);
  *            pairs: (1,4) (1,8) (1,16) (1,32) (2,8) (2,16) (4,8) (8,8) (32,4)
  *   warps    consumer warps per thread block (1..16)
  *   stages   shared-memory pipeline depth of the TMA kernel (0 = as many as fit)
- *   ctas     thread blocks per SM (TMA kernel) */
+ *   ctas     thread blocks per SM (TMA kernel); 0 = auto: 2 when two stages fit, else 1
+ * Once the pointer arrays exist and a device has been used, the values reported are the
+ * ones the next launch resolves to (stages and ctas filled in, a TMA kernel that does not
+ * fit replaced by the direct kernel). */
 int csrk_tuned_config(csrk_handle h, int32_t* kernel, int32_t* lanes, int32_t* unroll,
                       int32_t* warps, int32_t* stages, int32_t* ctas);
 
 /* csrk_set_config: force a launch configuration (same fields as csrk_tuned_config; a
  * negative field keeps the current value; a new lanes value without an unroll picks the
- * default unroll for it).  A forced TMA kernel whose super-super-rows do not fit two
- * shared-memory stages makes the compute calls return CSRK_ERR_UNSUPPORTED.  Used by the
- * autotuner and tests. */
+ * default unroll for it).  When kernel = 0 is given explicitly and the super-super-rows
+ * do not fit two shared-memory stages, the compute calls return CSRK_ERR_UNSUPPORTED;
+ * otherwise such a shape falls back to the direct kernel.  Used by the autotuner and
+ * tests. */
 int csrk_set_config(csrk_handle h, int32_t kernel, int32_t lanes, int32_t unroll,
                     int32_t warps, int32_t stages, int32_t ctas);
 

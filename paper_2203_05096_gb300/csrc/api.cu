@@ -7,6 +7,8 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <cstdio>
+#include <mutex>
 #include <new>
 #include <string>
 
@@ -50,6 +52,7 @@ struct csrk_matrix {
     TileStats stats;
     KernelConfig cfg;
     bool cfg_set = false;
+    bool kernel_forced = false;    // csrk_set_config asked for the TMA kernel explicitly
     unsigned long long timeout_ns = 2000000000ull;
 
     // device form
@@ -205,21 +208,22 @@ bool pair_compiled(int lanes, int unroll) {
     return false;
 }
 
-// Gather chunk for a lane count: the smallest compiled chunk that covers a lane's share of
-// the longest row (so a whole row's x gathers are in flight at once), capped at 32.
+// Gather chunk for a lane count: 8 (or 4 for rows of at most 4 entries per lane).  A
+// chunk of 8 keeps the TMA kernel at 56 registers, so two blocks of 16 consumer warps fit
+// on an SM; longer chunks only pay when a single block per SM is wanted.
 int default_unroll(int lanes, int max_row_len) {
     const int share = (max_row_len + lanes - 1) / std::max(1, lanes);
-    for (int u : {4, 8, 16, 32})
-        if (share <= u && pair_compiled(lanes, u)) return u;
-    for (int u : {32, 16, 8, 4})
-        if (pair_compiled(lanes, u)) return u;
-    return 4;
+    if (lanes == 32) return 4;
+    if (lanes == 1 && share <= 4) return 4;
+    return 8;
 }
 
 KernelConfig default_config(const csrk_matrix* h) {
     KernelConfig c;
     c.lanes = default_lanes(h);
     c.unroll = default_unroll(c.lanes, h->have_ptrs ? h->stats.max_row_len : 32);
+    c.warps = 16;
+    c.ctas = 0;   // auto: 2 blocks per SM when two stages fit, else 1
     return c;
 }
 
@@ -269,9 +273,12 @@ namespace {
 int resolve_config(csrk_matrix* h, int vt, KernelConfig& cfg, StagePlan& plan) {
     cfg = h->cfg_set ? h->cfg : default_config(h);
     plan = StagePlan{};
+    if (cfg.ctas == 0)
+        cfg.ctas = (cfg.kernel == 0 &&
+                    plan_stages(h->stats, (int)val_size(vt), smem_budget(h, 2), cfg.stages, plan)) ? 2 : 1;
     if (cfg.kernel == 0) {
         if (!plan_stages(h->stats, (int)val_size(vt), smem_budget(h, cfg.ctas), cfg.stages, plan)) {
-            if (h->cfg_set && h->cfg.kernel == 0)
+            if (h->kernel_forced)
                 return fail(CSRK_ERR_UNSUPPORTED, "super-super-rows too large for two shared-memory stages; "
                                                   "choose smaller sizes or the direct kernel");
             cfg.kernel = 1;   // the SSRs do not fit: fall back to direct loads
@@ -378,6 +385,194 @@ int compute(csrk_matrix* h, int32_t k, bool spmm, double alpha, const void* X, i
 
 }  // namespace
 
+// ================================================================== autotuner
+// Chooses super-row / super-super-row sizes and the launch shape by timing candidates on
+// the handle's own matrix (replacing the paper's constant-time model of Sec. 4.1, whose
+// Ampere-coefficient answer is one of the candidates).  Phase 1 times fixed size pairs
+// under the default launch shape; phase 2 times launch shapes on the three fastest size
+// pairs.  Results are cached per (n, nnz, longest row, dtype, device) in-process and, when
+// CSRK_TUNE_CACHE names a file, in that file.
+namespace {
+
+struct TunedChoice {
+    int32_t sr = 0, ssr = 0;
+    KernelConfig cfg;
+    float us = 0.f;
+};
+
+std::mutex g_tune_mu;
+std::vector<std::pair<std::string, TunedChoice>> g_tune_cache;
+bool g_tune_file_loaded = false;
+
+int install_pointers_impl(csrk_handle h, std::vector<int32_t>&& srp, std::vector<int32_t>&& ssrp);
+
+int set_fixed(csrk_matrix* h, int32_t sr, int32_t ssr) {
+    std::vector<int32_t> srp, ssrp;
+    fixed_pointers(h->m.n, sr, ssr, srp, ssrp);
+    int rc = install_pointers_impl(h, std::move(srp), std::move(ssrp));
+    if (rc) return rc;
+    h->sr = sr;
+    h->ssr = ssr;
+    return CSRK_OK;
+}
+
+std::string tune_key(const csrk_matrix* h) {
+    cudaDeviceProp prop{};
+    cudaGetDeviceProperties(&prop, h->device);
+    return std::to_string(h->m.n) + ":" + std::to_string(h->m.nnz()) + ":" +
+           std::to_string(h->stats.max_row_len) + ":" + std::to_string((int)h->dtype) + ":" +
+           std::to_string(h->num_sms) + ":" + std::string(prop.name);
+}
+
+void load_tune_file() {
+    if (g_tune_file_loaded) return;
+    g_tune_file_loaded = true;
+    const char* path = std::getenv("CSRK_TUNE_CACHE");
+    if (!path) return;
+    FILE* f = std::fopen(path, "r");
+    if (!f) return;
+    char key[512];
+    TunedChoice c;
+    while (std::fscanf(f, "%511s %d %d %d %d %d %d %d %d %f", key, &c.sr, &c.ssr, &c.cfg.kernel,
+                       &c.cfg.lanes, &c.cfg.unroll, &c.cfg.warps, &c.cfg.stages, &c.cfg.ctas, &c.us) == 10)
+        g_tune_cache.emplace_back(key, c);
+    std::fclose(f);
+}
+
+void save_tune_entry(const std::string& key, const TunedChoice& c) {
+    const char* path = std::getenv("CSRK_TUNE_CACHE");
+    if (!path) return;
+    FILE* f = std::fopen(path, "a");
+    if (!f) return;
+    std::string k = key;
+    for (auto& ch : k)
+        if (ch == ' ') ch = '_';
+    std::fprintf(f, "%s %d %d %d %d %d %d %d %d %.3f\n", k.c_str(), c.sr, c.ssr, c.cfg.kernel,
+                 c.cfg.lanes, c.cfg.unroll, c.cfg.warps, c.cfg.stages, c.cfg.ctas, c.us);
+    std::fclose(f);
+}
+
+int compute(csrk_matrix* h, int32_t k, bool spmm, double alpha, const void* X, int64_t ldx,
+            double beta, void* Y, int64_t ldy, unsigned flags, void* stream);
+
+float time_launches(csrk_matrix* h, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1, int reps) {
+    const unsigned fl = CSRK_VEC_PERMUTED;
+    for (int i = 0; i < 2; ++i)
+        if (compute(h, 1, false, 1.0, h->d_scratch[0], 1, 0.0, h->d_scratch[1], 1, fl, s)) return 1e30f;
+    cudaEventRecord(e0, s);
+    for (int i = 0; i < reps; ++i)
+        if (compute(h, 1, false, 1.0, h->d_scratch[0], 1, 0.0, h->d_scratch[1], 1, fl, s)) return 1e30f;
+    cudaEventRecord(e1, s);
+    if (cudaEventSynchronize(e1) != cudaSuccess) return 1e30f;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    return ms * 1000.f / reps;
+}
+
+int autotune(csrk_matrix* h) {
+    int rc;
+    if (h->m.n == 0) return set_fixed(h, 32, 8);
+    if ((rc = ensure_context(h))) return rc;
+    // sizes first so that the key can see the longest row
+    if ((rc = set_fixed(h, 32, 8))) return rc;
+    const std::string key = tune_key(h);
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        load_tune_file();
+        for (auto& e : g_tune_cache)
+            if (e.first == key) {
+                if ((rc = set_fixed(h, e.second.sr, e.second.ssr))) return rc;
+                h->cfg = e.second.cfg;
+                h->cfg_set = true;
+                h->kernel_forced = false;
+                return CSRK_OK;
+            }
+    }
+    const int vt = (int)h->dtype;
+    if ((rc = ensure_struct(h)) || (rc = ensure_vals(h, vt))) return rc;
+    const size_t vb = (size_t)h->m.n * 8;
+    if ((rc = ensure_scratch(h, 0, vb)) || (rc = ensure_scratch(h, 1, vb))) return rc;
+    CK_CUDA(cudaMemset(h->d_scratch[0], 0, vb), "tune memset");
+    cudaStream_t s;
+    CK_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking), "tune stream");
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int reps = 10;
+
+    std::vector<std::pair<int32_t, int32_t>> sizes = {{32, 1}, {32, 2}, {32, 4}, {32, 8}, {32, 16},
+                                                      {64, 1}, {64, 2}, {64, 4}, {64, 8}, {128, 1},
+                                                      {128, 2}, {16, 4}, {16, 8}, {16, 16}};
+    int32_t model_ssrs = 0, model_srs = 0;
+    const double rdens = (double)h->m.nnz() / h->m.n;
+    if (rdens > 0 && csrk_model_sizes(rdens, 1, &model_ssrs, &model_srs) == CSRK_OK && model_srs > 0 &&
+        model_ssrs > 0)
+        sizes.emplace_back(model_srs, model_ssrs);
+
+    std::vector<TunedChoice> phase1;
+    h->cfg_set = false;
+    h->kernel_forced = false;
+    for (auto& sz : sizes) {
+        if ((rc = set_fixed(h, sz.first, sz.second))) break;
+        if ((rc = ensure_struct(h))) break;
+        TunedChoice c;
+        c.sr = sz.first;
+        c.ssr = sz.second;
+        c.us = time_launches(h, s, e0, e1, reps);
+        StagePlan plan;
+        if (resolve_config(h, vt, c.cfg, plan)) continue;   // the shape the timing ran with
+        phase1.push_back(c);
+    }
+    std::sort(phase1.begin(), phase1.end(), [](auto& a, auto& b) { return a.us < b.us; });
+    TunedChoice best = phase1.empty() ? TunedChoice{} : phase1.front();
+
+    std::vector<std::pair<int, int>> pairs;
+    if (rdens <= 32) pairs = {{1, 4}, {1, 8}, {1, 16}, {2, 8}};
+    else if (rdens <= 64) pairs = {{2, 8}, {2, 16}, {4, 8}};
+    else pairs = {{4, 8}, {8, 8}, {32, 4}};
+    for (size_t b = 0; b < std::min<size_t>(3, phase1.size()) && rc == CSRK_OK; ++b) {
+        if ((rc = set_fixed(h, phase1[b].sr, phase1[b].ssr)) || (rc = ensure_struct(h))) break;
+        for (auto& pr : pairs)
+            for (int warps : {8, 16})
+                for (int kernel : {0, 1})
+                    for (int ctas : {1, 2}) {
+                        if (kernel == 1 && ctas == 2) continue;
+                        KernelConfig c;
+                        c.kernel = kernel;
+                        c.lanes = pr.first;
+                        c.unroll = pr.second;
+                        c.warps = warps;
+                        c.ctas = ctas;
+                        c.stages = 0;
+                        h->cfg = c;
+                        h->cfg_set = true;
+                        h->kernel_forced = (kernel == 0);
+                        const float us = time_launches(h, s, e0, e1, reps);
+                        if (us < best.us) {
+                            best.sr = phase1[b].sr;
+                            best.ssr = phase1[b].ssr;
+                            best.cfg = c;
+                            best.us = us;
+                        }
+                    }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamDestroy(s);
+    if (rc) return rc;
+    if (best.sr <= 0) return fail(CSRK_ERR_CUDA, "autotuning found no working configuration");
+    if ((rc = set_fixed(h, best.sr, best.ssr))) return rc;
+    h->cfg = best.cfg;
+    h->cfg_set = true;
+    h->kernel_forced = false;
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune_cache.emplace_back(key, best);
+    save_tune_entry(key, best);
+    return CSRK_OK;
+}
+
+}  // namespace
+
 // ================================================================== C ABI
 extern "C" {
 
@@ -433,7 +628,10 @@ int csrk_reorder(csrk_handle h, int method, int32_t* perm_out) {
     return CSRK_OK;
 }
 
-static int install_pointers(csrk_handle h, std::vector<int32_t>&& srp, std::vector<int32_t>&& ssrp) {
+}  // extern "C"
+
+namespace {
+int install_pointers_impl(csrk_handle h, std::vector<int32_t>&& srp, std::vector<int32_t>&& ssrp) {
     std::string err;
     if (!check_pointers(h->m.n, srp, ssrp, err)) return fail(CSRK_ERR_ARG, err);
     h->sr_ptr = std::move(srp);
@@ -443,15 +641,24 @@ static int install_pointers(csrk_handle h, std::vector<int32_t>&& srp, std::vect
     if (h->dev_ptrs) free_ptrs(h);   // pointer arrays changed: re-upload on next use
     return CSRK_OK;
 }
+}  // namespace
+
+extern "C" {
 
 int csrk_set_sizes(csrk_handle h, int32_t sr, int32_t ssr) {
     if (!h) return fail(CSRK_ERR_ARG, "handle is NULL");
-    if (sr == 0 && ssr == 0) return fail(CSRK_ERR_UNSUPPORTED, "autotuning is not available in this build");
+    if (sr == 0 && ssr == 0) {
+        try {
+            return autotune(h);
+        } catch (const std::bad_alloc&) {
+            return fail(CSRK_ERR_ALLOC, "out of host memory");
+        }
+    }
     if (sr <= 0 || ssr <= 0) return fail(CSRK_ERR_ARG, "sizes must be positive");
     try {
         std::vector<int32_t> srp, ssrp;
         fixed_pointers(h->m.n, sr, ssr, srp, ssrp);
-        int rc = install_pointers(h, std::move(srp), std::move(ssrp));
+        int rc = install_pointers_impl(h, std::move(srp), std::move(ssrp));
         if (rc) return rc;
     } catch (const std::bad_alloc&) {
         return fail(CSRK_ERR_ALLOC, "out of host memory");
@@ -466,7 +673,7 @@ int csrk_set_pointers(csrk_handle h, int32_t nsr, const int32_t* sr_ptr, int32_t
     if (!h) return fail(CSRK_ERR_ARG, "handle is NULL");
     if (nsr < 0 || nssr < 0 || !sr_ptr || !ssr_ptr) return fail(CSRK_ERR_ARG, "bad pointer arrays");
     try {
-        int rc = install_pointers(h, std::vector<int32_t>(sr_ptr, sr_ptr + nsr + 1),
+        int rc = install_pointers_impl(h, std::vector<int32_t>(sr_ptr, sr_ptr + nsr + 1),
                                   std::vector<int32_t>(ssr_ptr, ssr_ptr + nssr + 1));
         if (rc) return rc;
     } catch (const std::bad_alloc&) {
@@ -599,6 +806,14 @@ int csrk_tuned_config(csrk_handle h, int32_t* kernel, int32_t* lanes, int32_t* u
                       int32_t* warps, int32_t* stages, int32_t* ctas) {
     if (!h) return fail(CSRK_ERR_ARG, "handle is NULL");
     KernelConfig c = h->cfg_set ? h->cfg : default_config(h);
+    if (h->have_ptrs && h->smem_per_sm > 0) {   // device known: report what a launch will use
+        StagePlan plan;
+        KernelConfig r;
+        if (resolve_config(h, (int)h->dtype, r, plan) == CSRK_OK) {
+            c = r;
+            c.stages = c.kernel == 0 ? plan.stages : 0;
+        }
+    }
     if (kernel) *kernel = c.kernel;
     if (lanes) *lanes = c.lanes;
     if (unroll) *unroll = c.unroll;
@@ -615,6 +830,7 @@ int csrk_set_config(csrk_handle h, int32_t kernel, int32_t lanes, int32_t unroll
     if (kernel >= 0) {
         if (kernel > 1) return fail(CSRK_ERR_ARG, "kernel must be 0 or 1");
         c.kernel = kernel;
+        h->kernel_forced = (kernel == 0);
     }
     if (lanes >= 0) {
         if (lanes != 1 && lanes != 2 && lanes != 4 && lanes != 8 && lanes != 32)
@@ -635,7 +851,7 @@ int csrk_set_config(csrk_handle h, int32_t kernel, int32_t lanes, int32_t unroll
         c.stages = stages;
     }
     if (ctas >= 0) {
-        if (ctas < 1 || ctas > 4) return fail(CSRK_ERR_ARG, "ctas must be in [1, 4]");
+        if (ctas > 4) return fail(CSRK_ERR_ARG, "ctas must be 0 (auto) or in [1, 4]");
         c.ctas = ctas;
     }
     h->cfg = c;

@@ -156,16 +156,21 @@ __device__ __forceinline__ void report(int32_t* status, int32_t bit) {
     if (status) atomicOr(status, bit);
 }
 
+// Epilogue selector, uniform over a launch and decided on the host, so that no per-row
+// FP64 compare or multiply is issued when alpha == 1 or beta == 0.
+enum : int { EPI_SCALE = 1, EPI_ACCUM = 2 };   // alpha != 1, beta != 0
+
 // y = alpha*acc + beta*y in the accumulation precision; beta == 0 never reads y.
 template <typename XT, typename AT>
-__device__ __forceinline__ void store_y(XT* y, int64_t idx, AT acc, double alpha, double beta) {
+__device__ __forceinline__ void store_y(XT* y, int64_t idx, AT acc, double alpha, double beta,
+                                        int epi) {
     if constexpr (sizeof(AT) == 8) {
-        double r = alpha * acc;
-        if (beta != 0.0) r = fma(beta, x_f64(y[idx]), r);
+        double r = (epi & EPI_SCALE) ? alpha * acc : acc;
+        if (epi & EPI_ACCUM) r = fma(beta, x_f64(y[idx]), r);
         y[idx] = (XT)r;
     } else {
-        float r = (float)alpha * acc;
-        if (beta != 0.0) r = fmaf((float)beta, (float)y[idx], r);
+        float r = (epi & EPI_SCALE) ? (float)alpha * acc : acc;
+        if (epi & EPI_ACCUM) r = fmaf((float)beta, (float)y[idx], r);
         y[idx] = (XT)r;
     }
 }
@@ -174,30 +179,41 @@ __device__ __forceinline__ void store_y(XT* y, int64_t idx, AT acc, double alpha
 // One pass of a warp over up to 32/LPR rows [rb + lane/LPR ...] of a super-row.
 // col_s / val_s are indexable by absolute nonzero index (already offset).  Each lane walks
 // its row's nonzeros sub, sub+LPR, ... in chunks of U: it first issues the U independent
-// x gathers of the chunk (the long-latency loads, all in flight together), then runs the
-// chunk's U FMAs in stored order.
+// x gathers of a chunk (the long-latency loads, all in flight together), then runs the
+// chunk's U FMAs in stored order.  Full chunks carry no predicates; the last fewer-than-U
+// entries go in predicated chunks of T = U for U <= 8 (one round trip for short rows) and
+// T = 4 for longer chunks (at most 3 idle FP64 slots per row, where FP64 issue binds).
 template <typename VT, typename XT, typename AT, int LPR, int U>
 __device__ __forceinline__ void spmv_rows(int rb, int re, const int32_t* __restrict__ rp,
                                           const int32_t* __restrict__ col_s,
                                           const VT* __restrict__ val_s,
                                           const XT* __restrict__ x, XT* __restrict__ y,
-                                          double alpha, double beta, int lane) {
+                                          double alpha, double beta, int epi, int lane) {
     constexpr int RPP = 32 / LPR;   // rows per pass
+    constexpr int T = U <= 8 ? U : 4;
     const int sub = lane % LPR;
     for (int base = rb; base < re; base += RPP) {
         const int r = base + lane / LPR;
         AT acc = 0;
         if (r < re) {
             const int pe = rp[r + 1];
-            for (int c = rp[r] + sub; c < pe; c += U * LPR) {
+            int c = rp[r] + sub;
+            for (; c + (U - 1) * LPR < pe; c += U * LPR) {
                 XT xv[U];
 #pragma unroll
-                for (int t = 0; t < U; ++t) {
+                for (int t = 0; t < U; ++t) xv[t] = ldg_x(&x[col_s[c + t * LPR]]);
+#pragma unroll
+                for (int t = 0; t < U; ++t) acc = Acc<AT>::fma(val_s[c + t * LPR], xv[t], acc);
+            }
+            for (; c < pe; c += T * LPR) {
+                XT xv[T];
+#pragma unroll
+                for (int t = 0; t < T; ++t) {
                     const int p = c + t * LPR;
                     if (p < pe) xv[t] = ldg_x(&x[col_s[p]]);
                 }
 #pragma unroll
-                for (int t = 0; t < U; ++t) {
+                for (int t = 0; t < T; ++t) {
                     const int p = c + t * LPR;
                     if (p < pe) acc = Acc<AT>::fma(val_s[p], xv[t], acc);
                 }
@@ -208,7 +224,7 @@ __device__ __forceinline__ void spmv_rows(int rb, int re, const int32_t* __restr
             for (int off = LPR / 2; off > 0; off >>= 1)
                 acc += __shfl_xor_sync(0xffffffffu, acc, off);
         }
-        if (r < re && sub == 0) store_y<XT, AT>(y, r, acc, alpha, beta);
+        if (r < re && sub == 0) store_y<XT, AT>(y, r, acc, alpha, beta, epi);
     }
 }
 
@@ -220,7 +236,7 @@ __device__ __forceinline__ void spmm_rows(int rb, int re, const int32_t* __restr
                                           const VT* __restrict__ val_s,
                                           const XT* __restrict__ X, int64_t ldx,
                                           XT* __restrict__ Y, int64_t ldy, int k,
-                                          double alpha, double beta, int lane) {
+                                          double alpha, double beta, int epi, int lane) {
     constexpr int RPP = 32 / G;
     const int c0 = lane % G;
     for (int base = rb; base < re; base += RPP) {
@@ -243,7 +259,7 @@ __device__ __forceinline__ void spmm_rows(int rb, int re, const int32_t* __restr
 #pragma unroll
         for (int j = 0; j < CPL; ++j) {
             const int c = c0 + j * G;
-            if (c < k) store_y<XT, AT>(Y + (int64_t)r * ldy, c, acc[j], alpha, beta);
+            if (c < k) store_y<XT, AT>(Y + (int64_t)r * ldy, c, acc[j], alpha, beta, epi);
         }
     }
 }
@@ -261,6 +277,7 @@ struct TmaParams {
     int32_t k;
     int32_t nssr;
     double alpha, beta;
+    int32_t epi;   // EPI_SCALE | EPI_ACCUM
     int32_t* status;
     uint32_t off_srp, off_rp, off_col, off_val, stage_bytes, header_bytes;
     int32_t stages;
@@ -358,10 +375,11 @@ __global__ void __launch_bounds__(544, 1) csr3_tma_kernel(const TmaParams P) {
             const int sr = d.s0 + j;
             const int rb = srp[sr], re = srp[sr + 1];
             if constexpr (MODE == 0)
-                spmv_rows<VT, XT, AT, LPR, U>(rb, re, rp, col, val, x, y, P.alpha, P.beta, lane);
+                spmv_rows<VT, XT, AT, LPR, U>(rb, re, rp, col, val, x, y, P.alpha, P.beta, P.epi,
+                                              lane);
             else
                 spmm_rows<VT, XT, AT, LPR, U>(rb, re, rp, col, val, x, P.ldx, y, P.ldy, P.k,
-                                               P.alpha, P.beta, lane);
+                                               P.alpha, P.beta, P.epi, lane);
         }
         sr_seq += nsr;
         __syncwarp();
@@ -386,10 +404,10 @@ __global__ void __launch_bounds__(512, 1) csr3_direct_kernel(const TmaParams P) 
             const int rb = __ldg(&P.sr_ptr[sr]), re = __ldg(&P.sr_ptr[sr + 1]);
             if constexpr (MODE == 0)
                 spmv_rows<VT, XT, AT, LPR, U>(rb, re, P.rowptr, P.colidx, vals, x, y, P.alpha,
-                                              P.beta, lane);
+                                              P.beta, P.epi, lane);
             else
                 spmm_rows<VT, XT, AT, LPR, U>(rb, re, P.rowptr, P.colidx, vals, x, P.ldx, y,
-                                               P.ldy, P.k, P.alpha, P.beta, lane);
+                                               P.ldy, P.k, P.alpha, P.beta, P.epi, lane);
         }
     }
 }

@@ -36,7 +36,7 @@ __global__ void __launch_bounds__(256) csr3_static_kernel(
     int32_t nssr, const int32_t* __restrict__ ssr_ptr, const int32_t* __restrict__ sr_ptr,
     const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
     const double* __restrict__ vals, const double* __restrict__ x, double* __restrict__ y,
-    double alpha, double beta) {
+    double alpha, double beta, int epi) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int W = blockDim.x >> 5;
     for (int t = blockIdx.x; t < nssr; t += gridDim.x) {
@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(256) csr3_static_kernel(
         for (int sr = s0 + warp; sr < s1; sr += W) {
             const int rb = __ldg(&sr_ptr[sr]), re = __ldg(&sr_ptr[sr + 1]);
             csrk::dev::spmv_rows<double, double, double, 1, 8>(rb, re, rowptr, colidx, vals, x, y,
-                                                              alpha, beta, lane);
+                                                              alpha, beta, epi, lane);
         }
     }
 }
@@ -93,10 +93,11 @@ int csrk_spmv_static_scratch(int32_t n, int32_t nssr, const int32_t* ssr_ptr,
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     grid = (int)std::min<int64_t>(nssr, (int64_t)(sms > 0 ? sms : 1) * 8);
+    const int epi = (alpha != 1.0 ? csrk::dev::EPI_SCALE : 0) | (beta != 0.0 ? csrk::dev::EPI_ACCUM : 0);
     if (!perm) {   // no reordering: the kernel works on the caller's vectors directly
         if (grid > 0)
             csr3_static_kernel<<<grid, 256, 0, s>>>(nssr, ssr_ptr, sr_ptr, rowptr, colidx, vals, x, y,
-                                                    alpha, beta);
+                                                    alpha, beta, epi);
         cudaError_t e = cudaGetLastError();
         return e == cudaSuccess ? CSRK_OK : err(CSRK_ERR_CUDA, cudaGetErrorString(e));
     }
@@ -113,7 +114,7 @@ int csrk_spmv_static_scratch(int32_t n, int32_t nssr, const int32_t* ssr_ptr,
         return err(CSRK_ERR_CUDA, "permute y");
     if (grid > 0)
         csr3_static_kernel<<<grid, 256, 0, s>>>(nssr, ssr_ptr, sr_ptr, rowptr, colidx, vals, xp, yp,
-                                                alpha, beta);
+                                                alpha, beta, epi);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return err(CSRK_ERR_CUDA, cudaGetErrorString(e));
     if ((rc = csrk::launch_scatter_rows(yp, 1, y, 1, perm, n, 1, 8, s)))

@@ -296,3 +296,24 @@ def test_full_size_128cubed(points):
     ones = gpu_spmv(h, np.ones(lap.n))
     assert np.array_equal(ones, ospmv.csr_spmv(lap.n, lap.rowptr, lap.colidx, lap.vals, np.ones(lap.n)))
     csrk.destroy(h)
+
+
+# ------------------------------------------------------------------ autotuner
+def test_autotuner_picks_a_working_config():
+    a = small_27pt(13)
+    x = synth.uniform_vector(a.n, 25)
+    h = csrk.create(a.n, a.rowptr, a.colidx, a.vals)
+    csrk.reorder(h)
+    csrk.set_sizes(h, 0, 0)
+    inf = csrk.info(h)
+    cfg = csrk.tuned_config(h)
+    assert inf["sr"] > 0 and inf["ssr"] > 0 and inf["nssr"] > 0
+    assert cfg["kernel"] in (0, 1) and cfg["warps"] in (8, 16)
+    assert_close(gpu_spmv(h, x), a, a.vals, x)
+    # a second handle with the same shape reuses the cached choice
+    h2 = csrk.create(a.n, a.rowptr, a.colidx, a.vals)
+    csrk.reorder(h2)
+    csrk.set_sizes(h2, 0, 0)
+    assert csrk.tuned_config(h2) == cfg and csrk.info(h2)["sr"] == inf["sr"]
+    csrk.destroy(h)
+    csrk.destroy(h2)
