@@ -157,6 +157,35 @@ int csrk_spmm(csrk_handle h, int32_t k, double alpha, const void* X, int64_t ldx
 int csrk_permute(csrk_handle h, int direction, int32_t k, const void* in, int64_t ldi,
                  void* out, int64_t ldo, unsigned flags, void* stream);
 
+/* csrk_cg: solve A x = b for symmetric positive definite A by conjugate gradients on the
+ * CSR-k form (the paper names CG as the SpMV's consumer: Sec. 1, Sec. 7, Sec. 8), with
+ * x0 = 0 and the Hestenes-Stiefel recurrences.
+ *   b, x          DEVICE FP64 vectors of n entries, input numbering unless
+ *                 CSRK_VEC_PERMUTED; x receives the solution
+ *   rtol          stop when ||b - A x|| <= rtol ||b|| (the FP64 residual)
+ *   maxit         iteration limit (>= 1)
+ *   inner         CSRK_F64: plain FP64 CG (stops on the recursive residual, then checks
+ *                 the true one and resumes from it if needed); CSRK_F32 / CSRK_BF16: mixed
+ *                 precision -- q = A_lo p with values stored in that precision, p rounded to
+ *                 FP32 and FP32 accumulation, while vectors, dot products, alpha and beta
+ *                 stay FP64
+ *   replace_every mixed mode: recompute r = b - A x in FP64 every this many iterations
+ *                 (earlier once the recursive residual passes rtol/2)
+ *   restart       mixed mode: 0 keeps the direction across a replacement (reliable update)
+ *                 unless the recomputed residual exceeds twice the recursive one or the
+ *                 cycle diverged; 1 always restarts p = r (defect correction)
+ *   flags         0 or CSRK_VEC_PERMUTED
+ *   iters, relres optional outputs: iterations done and the final true relative residual
+ *   stream        cudaStream_t; the call returns after the solve (it reads a 64-byte state
+ *                 block from the device once per cycle)
+ * Iterations are recorded once into a CUDA graph (one cycle per graph) and replayed; all
+ * scalars stay on the device.  The first call allocates the solver workspace (7 vectors).
+ * Returns CSRK_OK when converged, CSRK_ERR_NOT_CONVERGED at maxit or on breakdown
+ * (p.q <= 0), with x holding the last iterate. */
+int csrk_cg(csrk_handle h, const double* b, double* x, double rtol, int32_t maxit,
+            csrk_dtype inner, int32_t replace_every, int32_t restart, unsigned flags,
+            int32_t* iters, double* relres, void* stream);
+
 /* csrk_destroy: free the handle and every host and device buffer it owns, after
  * synchronising the device.  NULL is a no-op. */
 int csrk_destroy(csrk_handle h);

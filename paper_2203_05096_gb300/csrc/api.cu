@@ -12,11 +12,12 @@
 #include <new>
 #include <string>
 
-#include "csrk_internal.h"
+#include "runtime.h"
 
 using namespace csrk;
 
-namespace {
+namespace csrk {
+namespace rt {
 
 thread_local std::string g_last_error;
 
@@ -28,52 +29,15 @@ int cuda_fail(cudaError_t e, const char* what) {
     return fail(CSRK_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
-#define CK_CUDA(call, what)                         \
-    do {                                            \
-        cudaError_t e_ = (call);                    \
-        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
-    } while (0)
-
 size_t val_size(int vt) { return vt == VAL_F64 ? 8 : (vt == VAL_F32 ? 4 : 2); }
 
-}  // namespace
+}  // namespace rt
+}  // namespace csrk
 
-void csrk::set_last_error(const std::string& msg) { g_last_error = msg; }
+void csrk::set_last_error(const std::string& msg) { csrk::rt::g_last_error = msg; }
 
-// ------------------------------------------------------------------ handle
-struct csrk_matrix {
-    CsrHost m;                     // current form (reordered after csrk_reorder)
-    std::vector<int32_t> perm;     // perm[new] = old; empty = identity
-    csrk_dtype dtype = CSRK_F64;
-    bool have_ptrs = false;
-    int32_t sr = 0, ssr = 0;       // fixed sizes (0 when given explicitly)
-    std::vector<int32_t> sr_ptr, ssr_ptr;
-    std::vector<SsrDesc> desc;
-    TileStats stats;
-    KernelConfig cfg;
-    bool cfg_set = false;
-    bool kernel_forced = false;    // csrk_set_config asked for the TMA kernel explicitly
-    unsigned long long timeout_ns = 2000000000ull;
-
-    // device form
-    int device = -1;
-    int num_sms = 0;
-    int smem_per_sm = 0, smem_optin = 0;
-    bool dev_struct = false;       // rowptr/colidx/perm uploaded
-    bool dev_ptrs = false;         // sr_ptr/desc uploaded
-    int32_t* d_rowptr = nullptr;
-    int32_t* d_colidx = nullptr;
-    void* d_vals[3] = {nullptr, nullptr, nullptr};
-    int32_t* d_sr_ptr = nullptr;
-    SsrDesc* d_desc = nullptr;
-    int32_t* d_perm = nullptr;
-    int32_t* d_status = nullptr;
-    // scratch: permuted x / y, and device copies of host vectors
-    void* d_scratch[4] = {nullptr, nullptr, nullptr, nullptr};
-    size_t scratch_bytes[4] = {0, 0, 0, 0};
-};
-
-namespace {
+namespace csrk {
+namespace rt {
 
 void free_ptrs(csrk_matrix* h) {
     cudaFree(h->d_sr_ptr);
@@ -94,6 +58,7 @@ void free_struct(csrk_matrix* h) {
 
 void free_device(csrk_matrix* h) {
     if (h->device < 0) return;
+    free_cg(h);
     free_struct(h);
     for (auto& v : h->d_vals) {
         cudaFree(v);
@@ -232,7 +197,8 @@ int smem_budget(const csrk_matrix* h, int ctas) {
     return std::min(per_cta, h->smem_optin);
 }
 
-}  // namespace
+}  // namespace rt
+}  // namespace csrk
 
 bool csrk::plan_stages(const TileStats& st, int val_bytes, int max_smem, int want_stages,
                        StagePlan& plan) {
@@ -267,7 +233,8 @@ int csrk::launch_csr3(const LaunchArgs& a, const KernelConfig& cfg, const StageP
     }
 }
 
-namespace {
+namespace csrk {
+namespace rt {
 
 // Resolve the launch configuration and stage plan for this handle and value type.
 int resolve_config(csrk_matrix* h, int vt, KernelConfig& cfg, StagePlan& plan) {
@@ -360,6 +327,7 @@ int compute(csrk_matrix* h, int32_t k, bool spmm, double alpha, const void* X, i
     a.nssr = (int32_t)h->desc.size();
     a.alpha = alpha;
     a.beta = beta;
+    a.skip = nullptr;
     a.status = h->d_status;
     a.stats = h->stats;
     a.val_type = vt;
@@ -383,7 +351,44 @@ int compute(csrk_matrix* h, int32_t k, bool spmm, double alpha, const void* X, i
     return CSRK_OK;
 }
 
-}  // namespace
+int launch_spmv_dev(csrk_matrix* h, int vt, const void* x, void* y, double alpha, double beta,
+                    bool x_f32, bool acc_f32, const int32_t* skip, cudaStream_t s) {
+    KernelConfig cfg;
+    StagePlan plan;
+    int rc;
+    if ((rc = resolve_config(h, vt, cfg, plan))) return rc;
+    LaunchArgs a{};
+    a.desc = h->d_desc;
+    a.sr_ptr = h->d_sr_ptr;
+    a.rowptr = h->d_rowptr;
+    a.colidx = h->d_colidx;
+    a.vals = h->d_vals[vt];
+    a.x = x;
+    a.y = y;
+    a.ldx = a.ldy = 1;
+    a.k = 1;
+    a.nssr = (int32_t)h->desc.size();
+    a.alpha = alpha;
+    a.beta = beta;
+    a.skip = skip;
+    a.status = h->d_status;
+    a.stats = h->stats;
+    a.val_type = vt;
+    a.x_f32 = x_f32;
+    a.acc_f32 = acc_f32;
+    a.spmm = false;
+    a.num_sms = h->num_sms;
+    a.timeout_ns = h->timeout_ns;
+    int e = launch_csr3(a, cfg, plan, s);
+    if (e == -1) return fail(CSRK_ERR_UNSUPPORTED, "kernel variant not compiled for this configuration");
+    if (e) return cuda_fail((cudaError_t)e, "CSR-3 kernel launch");
+    return CSRK_OK;
+}
+
+}  // namespace rt
+}  // namespace csrk
+
+using namespace csrk::rt;
 
 // ================================================================== autotuner
 // Chooses super-row / super-super-row sizes and the launch shape by timing candidates on
@@ -452,9 +457,6 @@ void save_tune_entry(const std::string& key, const TunedChoice& c) {
     std::fclose(f);
 }
 
-int compute(csrk_matrix* h, int32_t k, bool spmm, double alpha, const void* X, int64_t ldx,
-            double beta, void* Y, int64_t ldy, unsigned flags, void* stream);
-
 float time_launches(csrk_matrix* h, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1, int reps) {
     const unsigned fl = CSRK_VEC_PERMUTED;
     for (int i = 0; i < 2; ++i)
@@ -485,6 +487,7 @@ int autotune(csrk_matrix* h) {
                 h->cfg = e.second.cfg;
                 h->cfg_set = true;
                 h->kernel_forced = false;
+                h->generation++;
                 return CSRK_OK;
             }
     }
@@ -565,6 +568,7 @@ int autotune(csrk_matrix* h) {
     h->cfg = best.cfg;
     h->cfg_set = true;
     h->kernel_forced = false;
+    h->generation++;
     std::lock_guard<std::mutex> lock(g_tune_mu);
     g_tune_cache.emplace_back(key, best);
     save_tune_entry(key, best);
@@ -639,6 +643,7 @@ int install_pointers_impl(csrk_handle h, std::vector<int32_t>&& srp, std::vector
     build_descs(h->m, h->sr_ptr, h->ssr_ptr, h->desc, h->stats);
     h->have_ptrs = true;
     if (h->dev_ptrs) free_ptrs(h);   // pointer arrays changed: re-upload on next use
+    h->generation++;
     return CSRK_OK;
 }
 }  // namespace
@@ -856,6 +861,7 @@ int csrk_set_config(csrk_handle h, int32_t kernel, int32_t lanes, int32_t unroll
     }
     h->cfg = c;
     h->cfg_set = true;
+    h->generation++;
     return CSRK_OK;
 }
 

@@ -82,6 +82,7 @@ struct LaunchArgs {
     int32_t k;          // right-hand sides (1 for SpMV)
     int32_t nssr;
     double alpha, beta;
+    const int32_t* skip;  // optional device flag: non-zero makes the launch a no-op
     int32_t* status;
     TileStats stats;
     int val_type;       // ValType

@@ -278,6 +278,7 @@ struct TmaParams {
     int32_t nssr;
     double alpha, beta;
     int32_t epi;   // EPI_SCALE | EPI_ACCUM
+    const int32_t* skip;   // optional: non-zero on the device means "do nothing"
     int32_t* status;
     uint32_t off_srp, off_rp, off_col, off_val, stage_bytes, header_bytes;
     int32_t stages;
@@ -298,6 +299,7 @@ __device__ __forceinline__ void slice16(int64_t first, int64_t last_excl, int64_
 template <typename VT, typename XT, typename AT, int LPR, int MODE, int U>
 __global__ void __launch_bounds__(544, 1) csr3_tma_kernel(const TmaParams P) {
     extern __shared__ __align__(128) unsigned char smem[];
+    if (P.skip && *P.skip) return;   // uniform over the grid: every thread leaves together
     const int S = P.stages;
     uint64_t* full = reinterpret_cast<uint64_t*>(smem);
     uint64_t* empty = full + S;
@@ -393,6 +395,7 @@ __global__ void __launch_bounds__(544, 1) csr3_tma_kernel(const TmaParams P) {
 // as an autotuner alternative.
 template <typename VT, typename XT, typename AT, int LPR, int MODE, int U>
 __global__ void __launch_bounds__(512, 1) csr3_direct_kernel(const TmaParams P) {
+    if (P.skip && *P.skip) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int W = blockDim.x >> 5;
     const XT* __restrict__ x = static_cast<const XT*>(P.x);

@@ -26,6 +26,7 @@ static int launch_one(const LaunchArgs& a, const KernelConfig& cfg, const StageP
     P.alpha = a.alpha;
     P.beta = a.beta;
     P.epi = (a.alpha != 1.0 ? EPI_SCALE : 0) | (a.beta != 0.0 ? EPI_ACCUM : 0);
+    P.skip = a.skip;
     P.status = a.status;
     P.off_srp = plan.off_srp;
     P.off_rp = plan.off_rp;
@@ -39,8 +40,18 @@ static int launch_one(const LaunchArgs& a, const KernelConfig& cfg, const StageP
     if (cfg.kernel == 0) {
         auto kern = csr3_tma_kernel<VT, XT, AT, LPR, MODE, U>;
         const int smem = (int)(plan.header_bytes + (size_t)plan.stages * plan.stage_bytes);
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return (int)e;
+        // Raise the dynamic shared-memory limit to the device maximum once per device, so
+        // that later launches (including ones recorded into a CUDA graph) only launch.
+        static unsigned long long attr_set = 0;   // bit d: done on device d
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (dev >= 64 || !(__atomic_load_n(&attr_set, __ATOMIC_ACQUIRE) >> dev & 1ull)) {
+            int optin = 0;
+            cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+            if (e != cudaSuccess) return (int)e;
+            if (dev < 64) __atomic_fetch_or(&attr_set, 1ull << dev, __ATOMIC_ACQ_REL);
+        }
         const int threads = 32 * (cfg.warps + 1);
         int grid = a.num_sms * cfg.ctas;
         if (grid > a.nssr) grid = a.nssr;

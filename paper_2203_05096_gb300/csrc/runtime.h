@@ -1,0 +1,83 @@
+// Runtime internals shared by the C ABI (api.cu) and the solver (cg.cu): the handle and
+// the helpers that build its device form.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "csrk_internal.h"
+
+using csrk::CsrHost;
+using csrk::KernelConfig;
+using csrk::SsrDesc;
+using csrk::StagePlan;
+using csrk::TileStats;
+
+// The handle behind csrk_handle.
+struct csrk_matrix {
+    CsrHost m;                     // current form (reordered after csrk_reorder)
+    std::vector<int32_t> perm;     // perm[new] = old; empty = identity
+    csrk_dtype dtype = CSRK_F64;
+    bool have_ptrs = false;
+    int32_t sr = 0, ssr = 0;       // fixed sizes (0 when given explicitly)
+    std::vector<int32_t> sr_ptr, ssr_ptr;
+    std::vector<SsrDesc> desc;
+    TileStats stats;
+    KernelConfig cfg;
+    bool cfg_set = false;
+    bool kernel_forced = false;    // csrk_set_config asked for the TMA kernel explicitly
+    unsigned long long timeout_ns = 2000000000ull;
+
+    // device form
+    int device = -1;
+    int num_sms = 0;
+    int smem_per_sm = 0, smem_optin = 0;
+    bool dev_struct = false;       // rowptr/colidx/perm uploaded
+    bool dev_ptrs = false;         // sr_ptr/desc uploaded
+    int32_t* d_rowptr = nullptr;
+    int32_t* d_colidx = nullptr;
+    void* d_vals[3] = {nullptr, nullptr, nullptr};
+    int32_t* d_sr_ptr = nullptr;
+    SsrDesc* d_desc = nullptr;
+    int32_t* d_perm = nullptr;
+    int32_t* d_status = nullptr;
+    // scratch: permuted x / y, and device copies of host vectors
+    void* d_scratch[4] = {nullptr, nullptr, nullptr, nullptr};
+    size_t scratch_bytes[4] = {0, 0, 0, 0};
+    // conjugate-gradient workspace (cg.cu), allocated on the first solve
+    struct CgWork* cg = nullptr;
+    // bumped whenever pointers or the launch shape change (invalidates captured graphs)
+    unsigned long long generation = 0;
+};
+
+namespace csrk {
+namespace rt {
+
+int fail(int code, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+size_t val_size(int vt);
+int ensure_context(csrk_matrix* h);
+int ensure_struct(csrk_matrix* h);
+int ensure_vals(csrk_matrix* h, int vt);
+int ensure_scratch(csrk_matrix* h, int slot, size_t bytes);
+KernelConfig default_config(const csrk_matrix* h);
+int resolve_config(csrk_matrix* h, int vt, KernelConfig& cfg, StagePlan& plan);
+int compute(csrk_matrix* h, int32_t k, bool spmm, double alpha, const void* X, int64_t ldx,
+            double beta, void* Y, int64_t ldy, unsigned flags, void* stream);
+// The CSR-3 kernel alone on device vectors in the reordered numbering, with value type vt;
+// when skip is non-NULL and *skip != 0 at launch time on the device, the kernel exits at
+// once (used by captured solver iterations after convergence).
+void free_cg(csrk_matrix* h);
+int launch_spmv_dev(csrk_matrix* h, int vt, const void* x, void* y, double alpha, double beta,
+                    bool x_f32, bool acc_f32, const int32_t* skip, cudaStream_t s);
+
+}  // namespace rt
+}  // namespace csrk
+
+#define CK_CUDA(call, what)                                                  \
+    do {                                                                     \
+        cudaError_t e_ = (call);                                             \
+        if (e_ != cudaSuccess) return csrk::rt::cuda_fail(e_, what);         \
+    } while (0)

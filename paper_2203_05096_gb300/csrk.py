@@ -56,6 +56,7 @@ _PROTOS = {
     "csrk_tuned_config": [_vp, _pi32, _pi32, _pi32, _pi32, _pi32, _pi32],
     "csrk_set_config": [_vp, _i32, _i32, _i32, _i32, _i32, _i32],
     "csrk_device_status": [_vp, _vp, _pi32],
+    "csrk_cg": [_vp, _vp, _vp, _d, _i32, ctypes.c_int, _i32, _i32, _u, _pi32, ctypes.POINTER(_d), _vp],
     "csrk_spmv_static_scratch": [_i32, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _d, _vp, _d, _vp, _vp],
 }
 
@@ -221,6 +222,18 @@ def device_status(h, stream=None):
     if rc not in (0, 7):
         _check(rc, "csrk_device_status")
     return st.value
+
+
+def cg(h, b, x, rtol=1e-10, maxit=10000, inner="f64", replace_every=20, restart=0, flags=0,
+       stream=None, check=True):
+    """Solve A x = b; returns (status, iterations, true relative residual)."""
+    it = ctypes.c_int32()
+    rel = ctypes.c_double()
+    rc = lib().csrk_cg(h, _ptr(b), _ptr(x), float(rtol), int(maxit), DTYPES[inner], int(replace_every),
+                       int(restart), int(flags), ctypes.byref(it), ctypes.byref(rel), _stream(stream, b, x))
+    if check and rc not in (0, 8):
+        _check(rc, "csrk_cg")
+    return rc, it.value, rel.value
 
 
 def spmv_static_scratch(n, nssr, ssr_ptr, sr_ptr, rowptr, colidx, vals, perm, alpha, x, beta, y,
