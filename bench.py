@@ -322,6 +322,31 @@ def run_ours(args, world, rank, local):
                "h2d_bytes_per_step": int(sum(8 * s["a"].n for s in state)),
                "d2h_bytes_per_step": int(sum(8 * s["a"].n for s in state))}
 
+    # conjugate gradients to rtol 1e-10 on the 27-point matrix: FP64 against mixed precision
+    cg = None
+    if not args.no_cg:
+        s27 = state[-1]
+        b = torch.tensor(synth.uniform_vector(s27["a"].n, 5), dtype=torch.float64, device=dev)
+        xs = torch.empty_like(b)
+        cg = {"matrix": s27["name"], "rtol": 1e-10, "replace_every": 20, "runs": {}}
+        for inner, restart in (("f64", 0), ("f32", 0), ("bf16", 1)):
+            csrk.cg(s27["h"], b, xs, 1e-10, 5000, inner, 20, restart)     # capture the graphs
+            torch.cuda.synchronize()
+            times = []
+            for _ in range(3):
+                c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                c0.record(stream)
+                rc, iters, rel = csrk.cg(s27["h"], b, xs, 1e-10, 5000, inner, 20, restart)
+                c1.record(stream)
+                torch.cuda.synchronize()
+                times.append(c0.elapsed_time(c1))
+            cg["runs"][inner] = {"ms": round(min(times), 3), "ms_median": round(statistics.median(times), 3),
+                                 "iterations": iters, "true_relres": rel, "converged": rc == 0,
+                                 "restart": restart}
+        f64 = cg["runs"]["f64"]["ms"]
+        for k in ("f32", "bf16"):
+            cg["runs"][k]["speedup_vs_f64"] = round(f64 / cg["runs"][k]["ms"], 3)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         g, sample = cpu_oracle_gflops(mats, args.cpu_seconds)
@@ -353,6 +378,7 @@ def run_ours(args, world, rank, local):
                          "alg_bytes_per_launch": int(abytes), "peak_kind": peak_kind,
                          "kernel_hash": khash},
             "e2e": e2e,
+            "cg": cg,
             "gpu_launches": K * 3 * len(state),
             "clocks": clocks,
             "cpu_baseline": cpu,
@@ -434,6 +460,7 @@ def main():
     p.add_argument("--cpu-seconds", type=float, default=10.0)
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cg", action="store_true")
     p.add_argument("--side", type=int, default=SIDE, help="grid side (profiling runs use a smaller case)")
     p.add_argument("--only", choices=[m for m, _ in MATRICES], default=None)
     args = p.parse_args()

@@ -238,14 +238,16 @@ namespace rt {
 
 // Resolve the launch configuration and stage plan for this handle and value type.
 int resolve_config(csrk_matrix* h, int vt, KernelConfig& cfg, StagePlan& plan) {
-    cfg = h->cfg_set ? h->cfg : default_config(h);
+    // the tuned / forced shape belongs to the handle's own value type; other value types
+    // (the inner SpMV of a mixed-precision solve) start from the default shape
+    cfg = (h->cfg_set && vt == (int)h->dtype) ? h->cfg : default_config(h);
     plan = StagePlan{};
     if (cfg.ctas == 0)
         cfg.ctas = (cfg.kernel == 0 &&
                     plan_stages(h->stats, (int)val_size(vt), smem_budget(h, 2), cfg.stages, plan)) ? 2 : 1;
     if (cfg.kernel == 0) {
         if (!plan_stages(h->stats, (int)val_size(vt), smem_budget(h, cfg.ctas), cfg.stages, plan)) {
-            if (h->kernel_forced)
+            if (h->kernel_forced && vt == (int)h->dtype)
                 return fail(CSRK_ERR_UNSUPPORTED, "super-super-rows too large for two shared-memory stages; "
                                                   "choose smaller sizes or the direct kernel");
             cfg.kernel = 1;   // the SSRs do not fit: fall back to direct loads

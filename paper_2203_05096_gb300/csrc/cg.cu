@@ -24,12 +24,47 @@
 #include <cstring>
 #include <new>
 
+#include "kernels.cuh"
 #include "runtime.h"
 
 namespace {
 
 constexpr int RED_THREADS = 256;
-constexpr int MAX_RED_BLOCKS = 1024;
+constexpr int MAX_RED_BLOCKS = 2048;
+constexpr int ILP = 4;   // independent 16-byte accesses per thread per loop trip
+
+// Element-pair loop: calls pair(j) for pairs j (elements 2j, 2j+1) = start, start +
+// stride, ... < n/2, ILP pairs per trip with independent 16-byte loads, so each thread
+// keeps several memory requests in flight; then odd(n-1) for an odd last element.
+// Arrays are 256-byte aligned (cudaMalloc), so pairs are 16-byte aligned.
+template <typename PairF, typename OddF>
+__device__ __forceinline__ void for_pairs(int64_t n, PairF pair, OddF odd) {
+    const int64_t np = n >> 1;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    for (; j + (ILP - 1) * stride < np; j += ILP * stride) {
+#pragma unroll
+        for (int u = 0; u < ILP; ++u) pair(j + u * stride);
+    }
+    for (; j < np; j += stride) pair(j);
+    if ((n & 1) && blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) odd(n - 1);
+}
+
+__device__ __forceinline__ double2 ld2(const double* p, int64_t j) {
+    return reinterpret_cast<const double2*>(p)[j];
+}
+__device__ __forceinline__ void st2(double* p, int64_t j, double a, double b) {
+    reinterpret_cast<double2*>(p)[j] = make_double2(a, b);
+}
+__device__ __forceinline__ void ld2q(const double* q, int64_t j, double& a, double& b) {
+    const double2 v = reinterpret_cast<const double2*>(q)[j];
+    a = v.x;
+    b = v.y;
+}
+__device__ __forceinline__ void ld2q(const float* q, int64_t j, double& a, double& b);
+__device__ __forceinline__ void st2f(float* p, int64_t j, double a, double b) {
+    reinterpret_cast<float2*>(p)[j] = make_float2((float)a, (float)b);
+}
 
 struct CgState {
     double rr;        // r.r of the recursion
@@ -71,7 +106,7 @@ __device__ double block_sum(double v) {
     return t;
 }
 
-// Store the block partial; returns true (on thread 0 of exactly one block) when every
+// Store the block partial; returns true (for every thread of exactly one block) when every
 // block has stored, after which partials[0..gridDim.x) are complete and visible.
 __device__ bool last_block(double part, double* partials, uint32_t* counter) {
     __shared__ bool is_last;
@@ -85,15 +120,25 @@ __device__ bool last_block(double part, double* partials, uint32_t* counter) {
     return is_last;
 }
 
+// Sum of the block partials by all threads of the last block (thread 0 gets the total):
+// each thread adds a fixed strided subset, then the fixed block tree -- deterministic.
 __device__ double sum_partials(const double* partials) {
-    // in block order: deterministic
+    __threadfence();
     double t = 0.0;
-    for (int i = 0; i < (int)gridDim.x; ++i) t += ((volatile const double*)partials)[i];
-    return t;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) t += ((volatile const double*)partials)[i];
+    return block_sum(t);
 }
 
-template <typename T>
-__device__ __forceinline__ double as_f64(T v) { return (double)v; }
+// FP32 -> FP64 with integer instructions (a conversion instruction would occupy the FP64
+// pipe, which the dot products and updates already load).
+__device__ __forceinline__ double as_f64(double v) { return v; }
+__device__ __forceinline__ double as_f64(float v) { return csrk::dev::x_f64(v); }
+
+__device__ __forceinline__ void ld2q(const float* q, int64_t j, double& a, double& b) {
+    const float2 v = reinterpret_cast<const float2*>(q)[j];
+    a = as_f64(v.x);
+    b = as_f64(v.y);
+}
 
 // r = b, p = r (and p32), x = 0; b.b -> state
 __global__ void __launch_bounds__(RED_THREADS) cg_init(int32_t n, const double* __restrict__ b,
@@ -102,17 +147,25 @@ __global__ void __launch_bounds__(RED_THREADS) cg_init(int32_t n, const double* 
                                                        double rtol, int32_t maxit, int32_t keep_p,
                                                        CgState* st, double* partials) {
     double part = 0.0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    for_pairs(n, [&](int64_t j) {
+        const double2 bv = ld2(b, j);
+        st2(x, j, 0.0, 0.0);
+        st2(r, j, bv.x, bv.y);
+        st2(p, j, bv.x, bv.y);
+        if (p32) st2f(p32, j, bv.x, bv.y);
+        part += bv.x * bv.x + bv.y * bv.y;
+    }, [&](int64_t i) {
         const double bi = b[i];
         x[i] = 0.0;
         r[i] = bi;
         p[i] = bi;
         if (p32) p32[i] = (float)bi;
         part += bi * bi;
-    }
+    });
     part = block_sum(part);
-    if (last_block(part, partials, &st->counter) && threadIdx.x == 0) {
+    if (last_block(part, partials, &st->counter)) {
         const double bb = sum_partials(partials);
+        if (threadIdx.x != 0) return;
         st->bb = bb;
         st->rr = bb;
         st->rr_start = bb;
@@ -135,11 +188,16 @@ __global__ void __launch_bounds__(RED_THREADS) cg_dot_pq(int32_t n, const double
                                                          double* partials) {
     if (st->skip) return;
     double part = 0.0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        part += p[i] * as_f64(q[i]);
+    for_pairs(n, [&](int64_t j) {
+        const double2 pv = ld2(p, j);
+        double q0, q1;
+        ld2q(q, j, q0, q1);
+        part += pv.x * q0 + pv.y * q1;
+    }, [&](int64_t i) { part += p[i] * as_f64(q[i]); });
     part = block_sum(part);
-    if (last_block(part, partials, &st->counter) && threadIdx.x == 0) {
+    if (last_block(part, partials, &st->counter)) {
         const double pq = sum_partials(partials);
+        if (threadIdx.x != 0) return;
         st->pq = pq;
         if (!(pq > 0.0) || !isfinite(pq)) {
             st->done = 2;
@@ -161,15 +219,24 @@ __global__ void __launch_bounds__(RED_THREADS) cg_update_xr(int32_t n, double* _
     if (st->skip) return;
     const double alpha = st->alpha;
     double part = 0.0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    for_pairs(n, [&](int64_t j) {
+        const double2 pv = ld2(p, j), xv = ld2(x, j), rv = ld2(r, j);
+        double q0, q1;
+        ld2q(q, j, q0, q1);
+        const double r0 = rv.x - alpha * q0, r1 = rv.y - alpha * q1;
+        st2(x, j, xv.x + alpha * pv.x, xv.y + alpha * pv.y);
+        st2(r, j, r0, r1);
+        part += r0 * r0 + r1 * r1;
+    }, [&](int64_t i) {
         x[i] += alpha * p[i];
         const double ri = r[i] - alpha * as_f64(q[i]);
         r[i] = ri;
         part += ri * ri;
-    }
+    });
     part = block_sum(part);
-    if (last_block(part, partials, &st->counter) && threadIdx.x == 0) {
+    if (last_block(part, partials, &st->counter)) {
         const double rr_new = sum_partials(partials);
+        if (threadIdx.x != 0) return;
         st->beta = rr_new / st->rr;
         st->rr = rr_new;
         st->iters += 1;
@@ -199,19 +266,26 @@ __global__ void __launch_bounds__(RED_THREADS) cg_update_p(int32_t n, const doub
                                                            const CgState* st) {
     if (st->skip) return;
     const double beta = st->beta;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    for_pairs(n, [&](int64_t j) {
+        const double2 rv = ld2(r, j), pv = ld2(p, j);
+        const double p0 = rv.x + beta * pv.x, p1 = rv.y + beta * pv.y;
+        st2(p, j, p0, p1);
+        if (p32) st2f(p32, j, p0, p1);
+    }, [&](int64_t i) {
         const double pi = r[i] + beta * p[i];
         p[i] = pi;
         if (p32) p32[i] = (float)pi;
-    }
+    });
 }
 
 // Replacement, part 1: r = b (the FP64 SpMV then forms r = b - A x)
 __global__ void __launch_bounds__(RED_THREADS) cg_copy_b(int32_t n, const double* __restrict__ b,
                                                          double* __restrict__ r, const CgState* st) {
     if (st->done) return;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        r[i] = b[i];
+    for_pairs(n, [&](int64_t j) {
+        const double2 bv = ld2(b, j);
+        st2(r, j, bv.x, bv.y);
+    }, [&](int64_t i) { r[i] = b[i]; });
 }
 
 // Replacement, part 2: ||r||^2 of the recomputed residual; convergence test; decide
@@ -220,13 +294,17 @@ __global__ void __launch_bounds__(RED_THREADS) cg_replace_finish(int32_t n, cons
                                                                  CgState* st, double* partials) {
     if (st->done) return;
     double part = 0.0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    for_pairs(n, [&](int64_t j) {
+        const double2 rv = ld2(r, j);
+        part += rv.x * rv.x + rv.y * rv.y;
+    }, [&](int64_t i) {
         const double ri = r[i];
         part += ri * ri;
-    }
+    });
     part = block_sum(part);
-    if (last_block(part, partials, &st->counter) && threadIdx.x == 0) {
+    if (last_block(part, partials, &st->counter)) {
         const double rt = sum_partials(partials);
+        if (threadIdx.x != 0) return;
         st->rr_true = rt;
         if (rt <= st->tol2) {
             st->done = 1;
@@ -250,11 +328,15 @@ __global__ void __launch_bounds__(RED_THREADS) cg_restart_p(int32_t n, const dou
                                                             double* __restrict__ p, float* __restrict__ p32,
                                                             CgState* st) {
     if (st->done || !st->restart) return;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    for_pairs(n, [&](int64_t j) {
+        const double2 rv = ld2(r, j);
+        st2(p, j, rv.x, rv.y);
+        if (p32) st2f(p32, j, rv.x, rv.y);
+    }, [&](int64_t i) {
         const double ri = r[i];
         p[i] = ri;
         if (p32) p32[i] = (float)ri;
-    }
+    });
 }
 
 // the restart flag is consumed at the start of the next cycle
@@ -266,13 +348,18 @@ __global__ void cg_clear_restart(CgState* st) {
 __global__ void __launch_bounds__(RED_THREADS) cg_true_norm(int32_t n, const double* __restrict__ r,
                                                             CgState* st, double* partials) {
     double part = 0.0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    for_pairs(n, [&](int64_t j) {
+        const double2 rv = ld2(r, j);
+        part += rv.x * rv.x + rv.y * rv.y;
+    }, [&](int64_t i) {
         const double ri = r[i];
         part += ri * ri;
-    }
+    });
     part = block_sum(part);
-    if (last_block(part, partials, &st->counter) && threadIdx.x == 0) {
-        st->rr_true = sum_partials(partials);
+    if (last_block(part, partials, &st->counter)) {
+        const double rt = sum_partials(partials);
+        if (threadIdx.x != 0) return;
+        st->rr_true = rt;
         st->counter = 0;
     }
 }
@@ -281,8 +368,10 @@ __global__ void __launch_bounds__(RED_THREADS) cg_true_norm(int32_t n, const dou
 // from the recomputed residual with a fresh direction.
 __global__ void __launch_bounds__(RED_THREADS) cg_resume(int32_t n, const double* __restrict__ r,
                                                          double* __restrict__ p, CgState* st) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        p[i] = r[i];
+    for_pairs(n, [&](int64_t j) {
+        const double2 rv = ld2(r, j);
+        st2(p, j, rv.x, rv.y);
+    }, [&](int64_t i) { p[i] = r[i]; });
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         st->rr = st->rr_true;
         st->rr_start = st->rr_true;
@@ -358,6 +447,8 @@ int alloc_cg(csrk_matrix* h) {
         free_cg(h);
         return fail(CSRK_ERR_ALLOC, std::string("CG workspace: ") + cudaGetErrorString(e));
     }
+    // 4 blocks of 256 per SM, each thread keeping ILP 16-byte loads per array in flight;
+    // for n up to ~4.9M every thread runs at most one full ILP trip plus a short tail
     w->grid = std::min(MAX_RED_BLOCKS, std::max(1, h->num_sms * 4));
     return CSRK_OK;
 }

@@ -181,8 +181,8 @@ __device__ __forceinline__ void store_y(XT* y, int64_t idx, AT acc, double alpha
 // its row's nonzeros sub, sub+LPR, ... in chunks of U: it first issues the U independent
 // x gathers of a chunk (the long-latency loads, all in flight together), then runs the
 // chunk's U FMAs in stored order.  Full chunks carry no predicates; the last fewer-than-U
-// entries go in predicated chunks of T = U for U <= 8 (one round trip for short rows) and
-// T = 4 for longer chunks (at most 3 idle FP64 slots per row, where FP64 issue binds).
+// entries go in predicated chunks of 4, so a row issues at most 3 idle FP64 slots (wider
+// tail chunks measured slower on the 27-point stencil, where FP64 issue binds).
 template <typename VT, typename XT, typename AT, int LPR, int U>
 __device__ __forceinline__ void spmv_rows(int rb, int re, const int32_t* __restrict__ rp,
                                           const int32_t* __restrict__ col_s,
@@ -190,7 +190,7 @@ __device__ __forceinline__ void spmv_rows(int rb, int re, const int32_t* __restr
                                           const XT* __restrict__ x, XT* __restrict__ y,
                                           double alpha, double beta, int epi, int lane) {
     constexpr int RPP = 32 / LPR;   // rows per pass
-    constexpr int T = U <= 8 ? U : 4;
+    constexpr int T = U < 4 ? U : 4;
     const int sub = lane % LPR;
     for (int base = rb; base < re; base += RPP) {
         const int r = base + lane / LPR;
@@ -296,8 +296,10 @@ __device__ __forceinline__ void slice16(int64_t first, int64_t last_excl, int64_
 
 // MODE 0: SpMV with LPR lanes per row and gather chunks of U.  MODE 1: SpMM with G = LPR
 // lanes per row and U columns per lane.
+// At most 60 registers per thread, so two blocks of 16 consumer warps + 1 producer warp
+// fit on one SM (65,536 registers).
 template <typename VT, typename XT, typename AT, int LPR, int MODE, int U>
-__global__ void __launch_bounds__(544, 1) csr3_tma_kernel(const TmaParams P) {
+__global__ void __launch_bounds__(544, 2) csr3_tma_kernel(const TmaParams P) {
     extern __shared__ __align__(128) unsigned char smem[];
     if (P.skip && *P.skip) return;   // uniform over the grid: every thread leaves together
     const int S = P.stages;
