@@ -186,6 +186,57 @@ int csrk_cg(csrk_handle h, const double* b, double* x, double rtol, int32_t maxi
             csrk_dtype inner, int32_t replace_every, int32_t restart, unsigned flags,
             int32_t* iters, double* relres, void* stream);
 
+/* ---------------------------------------------------------------- batches
+ * Many matrices of uneven size handled by single launches (the library's batched mode;
+ * the paper runs one matrix at a time).  A batch refers to its handles' device forms:
+ * keep the handles alive and leave their sizes and pointers unchanged while the batch
+ * exists.  All batched vectors are FP64, row-major n_i x k_i blocks (leading dimension
+ * k_i), in each matrix's reordered numbering (csrk_permute moves vectors there). */
+
+/* csrk_batch_create: build the work list of a batch.
+ *   hs     count handles, each with its pointer arrays set (sizes or explicit); any
+ *          value dtype; all on the current device
+ *   k      right-hand sides per matrix, 1..64
+ * Tiles of about 32K nonzeros (whole super-super-rows) are sorted by decreasing work.
+ * Uploads the handles' device forms if needed.  Errors: CSRK_ERR_ARG, CSRK_ERR_STATE,
+ * CSRK_ERR_ALLOC, CSRK_ERR_CUDA. */
+int csrk_batch_create(const csrk_handle* hs, int32_t count, const int32_t* k,
+                      csrk_batch_handle* out);
+
+/* csrk_batch_spmm: Y_i = alpha A_i X_i + beta Y_i for every matrix of the batch in one
+ * persistent launch (blocks take tiles from an atomic counter; no block waits on another).
+ *   X, Y    host arrays of count DEVICE pointers (X[i], Y[i]: n_i x k_i FP64 blocks)
+ *   flags   must be CSRK_VEC_PERMUTED
+ * A call with the same pointers as the previous one reuses the device-side table (one
+ * launch, no copy); new pointers cost one small host-to-device copy first. */
+int csrk_batch_spmm(csrk_batch_handle b, double alpha, const void* const* X, double beta,
+                    void* const* Y, unsigned flags, void* stream);
+
+/* csrk_batch_cg: independent CG solves A_i x = b for every (matrix, right-hand side) of the
+ * batch, FP64 vectors and scalars, q = A_i p with each matrix's stored values (FP32-stored
+ * matrices give FP32-valued operators).  Exactly `iters` iterations run, recorded once in
+ * a CUDA graph (re-recorded when iters changes) and replayed; a system whose recursive
+ * residual reaches rtol stops updating.
+ *   B, X       host arrays of count DEVICE pointers (n_i x k_i FP64 blocks, reordered
+ *              numbering); X receives the solutions (x0 = 0)
+ *   k_i        must be a power of two <= 32
+ *   relres     optional host array of (sum of k_i) FP64: final true ||b - A x|| / ||b||
+ *              per system, systems ordered by matrix then column
+ *   iters_done optional host array of (sum of k_i): iterations each system performed
+ * Synchronous: returns when the results are on the host. */
+int csrk_batch_cg(csrk_batch_handle b, const double* const* B, double* const* X,
+                  int32_t iters, double rtol, double* relres, int32_t* iters_done,
+                  void* stream);
+
+/* csrk_batch_info: matrices, systems (sum of k_i), tiles, and elements of one
+ * concatenated vector (sum of n_i k_i); any pointer may be NULL. */
+int csrk_batch_info(csrk_batch_handle b, int32_t* nmat, int32_t* nsys, int32_t* ntiles,
+                    int64_t* total);
+
+/* csrk_batch_destroy: free the batch (not its handles) after synchronising the device.
+ * NULL is a no-op. */
+int csrk_batch_destroy(csrk_batch_handle b);
+
 /* csrk_destroy: free the handle and every host and device buffer it owns, after
  * synchronising the device.  NULL is a no-op. */
 int csrk_destroy(csrk_handle h);

@@ -1,0 +1,585 @@
+// Batched work over many CSR-k matrices of uneven size.
+//
+// csrk_batch_spmm: Y_i = alpha A_i X_i + beta Y_i for every matrix i of a batch in ONE
+// persistent launch.  The work list holds tiles (matrix, range of super-super-rows),
+// sorted by decreasing work; each thread block takes the next tile with an atomic counter
+// (no block ever waits for another) and runs the tile's super-rows on its warps, with the
+// row mapping of the matrix's right-hand-side count (one row per lane for k = 1, k lanes
+// per row otherwise).  The last block to finish resets the counter, so the launch can be
+// replayed from a CUDA graph.
+//
+// csrk_batch_cg: independent conjugate-gradient solves for every (matrix, right-hand side)
+// pair, FP64 vectors and scalars, each step one batched SpMM launch plus batched vector
+// kernels; a fixed number of iterations is recorded once into a CUDA graph and replayed.
+// A system whose recursive residual reaches rtol freezes (alpha = 0).  Reductions are
+// deterministic: per-chunk partials, then one warp per system summing its chunks in order.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "kernels.cuh"
+#include "runtime.h"
+
+namespace {
+
+using csrk::dev::bf16_t;
+
+struct BatchMat {
+    const int32_t* rowptr;
+    const int32_t* colidx;
+    const void* vals;
+    const int32_t* sr_ptr;
+    const SsrDesc* desc;
+    const double* X;
+    double* Y;
+    int32_t n, k, vt, pad;
+};
+
+struct BatchTile {
+    int32_t mat, t0, t1, pad;
+};
+
+struct Chunk {   // contiguous rows of one matrix for the batched vector kernels
+    int32_t mat, row0, row1, pad;
+    int64_t off;  // element offset of row0 in the concatenated vectors
+};
+
+constexpr int BW = 8;   // warps per block of the persistent SpMM
+
+template <typename VT>
+__device__ __forceinline__ void tile_rows(const BatchMat& m, int rb, int re, double alpha, double beta,
+                                          int epi, int lane) {
+    const VT* vals = static_cast<const VT*>(m.vals);
+    using namespace csrk::dev;
+    switch (m.k) {
+        case 1:
+            spmv_rows<VT, double, double, 1, 8>(rb, re, m.rowptr, m.colidx, vals, m.X, m.Y, alpha, beta, epi, lane);
+            break;
+        case 2:
+            spmm_rows<VT, double, double, 2, 1>(rb, re, m.rowptr, m.colidx, vals, m.X, 2, m.Y, 2, 2, alpha, beta, epi, lane);
+            break;
+        case 3:
+        case 4:
+            spmm_rows<VT, double, double, 4, 1>(rb, re, m.rowptr, m.colidx, vals, m.X, m.k, m.Y, m.k, m.k, alpha, beta, epi, lane);
+            break;
+        case 5: case 6: case 7: case 8:
+            spmm_rows<VT, double, double, 8, 1>(rb, re, m.rowptr, m.colidx, vals, m.X, m.k, m.Y, m.k, m.k, alpha, beta, epi, lane);
+            break;
+        default:
+            if (m.k <= 16)
+                spmm_rows<VT, double, double, 16, 1>(rb, re, m.rowptr, m.colidx, vals, m.X, m.k, m.Y, m.k, m.k, alpha, beta, epi, lane);
+            else if (m.k <= 32)
+                spmm_rows<VT, double, double, 32, 1>(rb, re, m.rowptr, m.colidx, vals, m.X, m.k, m.Y, m.k, m.k, alpha, beta, epi, lane);
+            else
+                spmm_rows<VT, double, double, 32, 2>(rb, re, m.rowptr, m.colidx, vals, m.X, m.k, m.Y, m.k, m.k, alpha, beta, epi, lane);
+    }
+}
+
+__global__ void __launch_bounds__(BW * 32) batch_spmm_kernel(const BatchMat* __restrict__ mats,
+                                                             const BatchTile* __restrict__ tiles,
+                                                             int32_t ntiles, uint32_t* counters,
+                                                             double alpha, double beta, int epi) {
+    __shared__ int32_t tile_id;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (;;) {
+        if (threadIdx.x == 0) tile_id = (int32_t)atomicAdd(&counters[0], 1u);
+        __syncthreads();
+        const int32_t t = tile_id;
+        __syncthreads();
+        if (t >= ntiles) break;
+        const BatchTile tl = tiles[t];
+        const BatchMat m = mats[tl.mat];
+        for (int32_t q = tl.t0; q < tl.t1; ++q) {
+            const SsrDesc d = m.desc[q];
+            for (int sr = d.s0 + warp; sr < d.s1; sr += BW) {
+                const int rb = m.sr_ptr[sr], re = m.sr_ptr[sr + 1];
+                switch (m.vt) {
+                    case csrk::VAL_F64: tile_rows<double>(m, rb, re, alpha, beta, epi, lane); break;
+                    case csrk::VAL_F32: tile_rows<float>(m, rb, re, alpha, beta, epi, lane); break;
+                    default: tile_rows<bf16_t>(m, rb, re, alpha, beta, epi, lane); break;
+                }
+            }
+        }
+    }
+    // the last block out resets the tile counter for the next launch
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&counters[1], 1u) == gridDim.x - 1) {
+            atomicExch(&counters[0], 0u);
+            atomicExch(&counters[1], 0u);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- batched CG kernels
+constexpr int VT_THREADS = 256;   // vector-kernel block; a multiple of every k (power of two <= 32)
+
+struct SysState {   // per (matrix, right-hand side)
+    double rr, pq, alpha, beta, bb, tol2;
+    int32_t frozen, iters;
+};
+
+// Per-chunk, per-column partial sums of a[i]*b[i] over the chunk's elements.  With k a
+// power of two dividing the block size, thread t always sees column t % k.
+__device__ void chunk_partial(double v, int k, double* out /* k entries */) {
+    __shared__ double red[VT_THREADS / 32][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int off = 16; off >= k && off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if (lane < k) red[warp][lane] = v;
+    __syncthreads();
+    if (threadIdx.x < k) {
+        double t = 0.0;
+        for (int w = 0; w < VT_THREADS / 32; ++w) t += red[w][threadIdx.x];
+        out[threadIdx.x] = t;
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ int sys_of(const int32_t* sys_off, int mat, int c) { return sys_off[mat] + c; }
+
+// B -> R, P; X = 0; partial b.b
+__global__ void __launch_bounds__(VT_THREADS) bcg_init(const Chunk* __restrict__ chunks, const BatchMat* mats,
+                                                       const double* __restrict__ Bv, double* X, double* R,
+                                                       double* P, double* partials) {
+    const Chunk ch = chunks[blockIdx.x];
+    const int k = mats[ch.mat].k;
+    const int64_t e0 = ch.off, e1 = ch.off + (int64_t)(ch.row1 - ch.row0) * k;
+    double v = 0.0;
+    for (int64_t e = e0 + threadIdx.x; e < e1; e += VT_THREADS) {
+        const double b = Bv[e];
+        X[e] = 0.0;
+        R[e] = b;
+        P[e] = b;
+        v += b * b;
+    }
+    chunk_partial(v, k, partials + (int64_t)blockIdx.x * 32);
+}
+
+__global__ void __launch_bounds__(VT_THREADS) bcg_dot(const Chunk* __restrict__ chunks, const BatchMat* mats,
+                                                      const double* __restrict__ A, const double* __restrict__ Bv,
+                                                      double* partials) {
+    const Chunk ch = chunks[blockIdx.x];
+    const int k = mats[ch.mat].k;
+    const int64_t e0 = ch.off, e1 = ch.off + (int64_t)(ch.row1 - ch.row0) * k;
+    double v = 0.0;
+    for (int64_t e = e0 + threadIdx.x; e < e1; e += VT_THREADS) v += A[e] * Bv[e];
+    chunk_partial(v, k, partials + (int64_t)blockIdx.x * 32);
+}
+
+// X += alpha P; R -= alpha Q; partial r.r
+__global__ void __launch_bounds__(VT_THREADS) bcg_update_xr(const Chunk* __restrict__ chunks, const BatchMat* mats,
+                                                            const int32_t* sys_off, const SysState* st,
+                                                            double* X, double* R, const double* __restrict__ P,
+                                                            const double* __restrict__ Q, double* partials) {
+    const Chunk ch = chunks[blockIdx.x];
+    const int k = mats[ch.mat].k;
+    const int64_t e0 = ch.off, e1 = ch.off + (int64_t)(ch.row1 - ch.row0) * k;
+    const double alpha = st[sys_of(sys_off, ch.mat, threadIdx.x % k)].alpha;
+    double v = 0.0;
+    for (int64_t e = e0 + threadIdx.x; e < e1; e += VT_THREADS) {
+        X[e] += alpha * P[e];
+        const double r = R[e] - alpha * Q[e];
+        R[e] = r;
+        v += r * r;
+    }
+    chunk_partial(v, k, partials + (int64_t)blockIdx.x * 32);
+}
+
+// P = R + beta P
+__global__ void __launch_bounds__(VT_THREADS) bcg_update_p(const Chunk* __restrict__ chunks, const BatchMat* mats,
+                                                           const int32_t* sys_off, const SysState* st,
+                                                           const double* __restrict__ R, double* P) {
+    const Chunk ch = chunks[blockIdx.x];
+    const int k = mats[ch.mat].k;
+    const int64_t e0 = ch.off, e1 = ch.off + (int64_t)(ch.row1 - ch.row0) * k;
+    const double beta = st[sys_of(sys_off, ch.mat, threadIdx.x % k)].beta;
+    for (int64_t e = e0 + threadIdx.x; e < e1; e += VT_THREADS) P[e] = R[e] + beta * P[e];
+}
+
+// One warp per system: sum the system's chunk partials in chunk order (lanes stride, then
+// a fixed shuffle tree), then apply `stage`:
+//   0: b.b (init)   1: p.q -> alpha   2: r.r -> beta, freeze when converged   3: true r.r
+__global__ void bcg_finalize(const int32_t* sys_mat, const int32_t* sys_col, const int32_t* mat_chunk0,
+                             const int32_t* mat_chunk1, const double* partials, SysState* st, int32_t nsys,
+                             int stage, double rtol, double* out_true) {
+    const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (s >= nsys) return;
+    const int m = sys_mat[s], c = sys_col[s];
+    double t = 0.0;
+    for (int q = mat_chunk0[m] + lane; q < mat_chunk1[m]; q += 32) t += partials[(int64_t)q * 32 + c];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+    if (lane != 0) return;
+    SysState& y = st[s];
+    if (stage == 0) {
+        y.bb = t;
+        y.rr = t;
+        y.tol2 = rtol * rtol * t;
+        y.frozen = (t == 0.0);
+        y.iters = 0;
+        y.alpha = 0.0;
+        y.beta = 0.0;
+    } else if (stage == 1) {
+        y.pq = t;
+        y.alpha = (y.frozen || !(t > 0.0)) ? 0.0 : y.rr / t;
+        if (!(t > 0.0)) y.frozen = 1;
+    } else if (stage == 2) {
+        if (y.frozen) {
+            y.beta = 0.0;
+            return;
+        }
+        y.beta = t / y.rr;
+        y.rr = t;
+        y.iters += 1;
+        if (t <= y.tol2) {
+            y.frozen = 1;
+            y.beta = 0.0;
+        }
+    } else {
+        out_true[s] = y.bb > 0.0 ? sqrt(t / y.bb) : 0.0;
+    }
+}
+
+// copy between the user's per-matrix blocks and the concatenated buffer
+__global__ void bcg_gather(const double* const* src, const int64_t* moff, const int64_t* mlen, int32_t nmat,
+                           double* dst) {
+    for (int m = blockIdx.y; m < nmat; m += gridDim.y)
+        for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < mlen[m]; e += (int64_t)gridDim.x * blockDim.x)
+            dst[moff[m] + e] = src[m][e];
+}
+__global__ void bcg_scatter(const double* src, const int64_t* moff, const int64_t* mlen, int32_t nmat,
+                            double* const* dst) {
+    for (int m = blockIdx.y; m < nmat; m += gridDim.y)
+        for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < mlen[m]; e += (int64_t)gridDim.x * blockDim.x)
+            dst[m][e] = src[moff[m] + e];
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ the batch object
+struct csrk_batch {
+    std::vector<csrk_handle> hs;
+    std::vector<int32_t> k;
+    int device = -1;
+    int num_sms = 0;
+    int32_t nmat = 0, ntiles = 0, nchunks = 0, nsys = 0;
+    int64_t total = 0;               // elements of one concatenated vector block
+    BatchMat* d_mats_user = nullptr; // tables: user-bound vectors / internal P,Q / internal X,R
+    BatchMat* d_mats_pq = nullptr;
+    BatchMat* d_mats_xr = nullptr;
+    BatchTile* d_tiles = nullptr;
+    uint32_t* d_counters = nullptr;
+    Chunk* d_chunks = nullptr;
+    int32_t *d_sys_mat = nullptr, *d_sys_col = nullptr, *d_sys_off = nullptr;
+    int32_t *d_mat_chunk0 = nullptr, *d_mat_chunk1 = nullptr;
+    int64_t *d_moff = nullptr, *d_mlen = nullptr;
+    std::vector<BatchMat> h_mats;
+    std::vector<const void*> bound_x;
+    std::vector<void*> bound_y;
+    BatchMat* h_pinned_mats = nullptr;
+    // CG buffers
+    double *B = nullptr, *X = nullptr, *R = nullptr, *P = nullptr, *Q = nullptr, *partials = nullptr;
+    SysState* st = nullptr;
+    double* d_true = nullptr;
+    const double** d_ptrs_in = nullptr;
+    double** d_ptrs_out = nullptr;
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int32_t exec_iters = 0;
+    double exec_rtol = 0.0;
+};
+
+namespace {
+using namespace csrk::rt;
+
+template <typename T>
+int dmalloc(T** p, size_t count) {
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), std::max<size_t>(count, 1) * sizeof(T));
+    return e == cudaSuccess ? CSRK_OK : fail(CSRK_ERR_ALLOC, std::string("batch cudaMalloc: ") + cudaGetErrorString(e));
+}
+template <typename T>
+int upload(T** p, const std::vector<T>& v) {
+    int rc = dmalloc(p, v.size());
+    if (rc) return rc;
+    if (!v.empty()) CK_CUDA(cudaMemcpy(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice), "batch upload");
+    return CSRK_OK;
+}
+
+void batch_free(csrk_batch* b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    for (void* p : {(void*)b->d_mats_user, (void*)b->d_mats_pq, (void*)b->d_mats_xr, (void*)b->d_tiles,
+                    (void*)b->d_counters, (void*)b->d_chunks, (void*)b->d_sys_mat, (void*)b->d_sys_col,
+                    (void*)b->d_sys_off, (void*)b->d_mat_chunk0, (void*)b->d_mat_chunk1, (void*)b->d_moff,
+                    (void*)b->d_mlen, (void*)b->B, (void*)b->X, (void*)b->R, (void*)b->P, (void*)b->Q,
+                    (void*)b->partials, (void*)b->st, (void*)b->d_true, (void*)b->d_ptrs_in,
+                    (void*)b->d_ptrs_out})
+        cudaFree(p);
+    if (b->h_pinned_mats) cudaFreeHost(b->h_pinned_mats);
+    if (b->cap) cudaStreamDestroy(b->cap);
+}
+
+int launch_batch_spmm(csrk_batch* b, const BatchMat* table, double alpha, double beta, cudaStream_t s) {
+    const int epi = (alpha != 1.0 ? csrk::dev::EPI_SCALE : 0) | (beta != 0.0 ? csrk::dev::EPI_ACCUM : 0);
+    const int grid = std::min<int>(b->ntiles, std::max(1, b->num_sms * 4));
+    if (grid == 0) return CSRK_OK;
+    batch_spmm_kernel<<<grid, BW * 32, 0, s>>>(table, b->d_tiles, b->ntiles, b->d_counters, alpha, beta, epi);
+    CK_CUDA(cudaGetLastError(), "batch SpMM launch");
+    return CSRK_OK;
+}
+
+int fill_table(csrk_batch* b, BatchMat* table, const double* xbase, double* ybase) {
+    std::vector<BatchMat> t = b->h_mats;
+    int64_t off = 0;
+    for (int32_t i = 0; i < b->nmat; ++i) {
+        t[i].X = xbase + off;
+        t[i].Y = ybase + off;
+        off += (int64_t)t[i].n * t[i].k;
+    }
+    CK_CUDA(cudaMemcpy(table, t.data(), t.size() * sizeof(BatchMat), cudaMemcpyHostToDevice), "batch table");
+    return CSRK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int csrk_batch_create(const csrk_handle* hs, int32_t count, const int32_t* k, csrk_batch_handle* out) {
+    if (!out || !hs || !k || count < 1) return fail(CSRK_ERR_ARG, "bad batch arguments");
+    *out = nullptr;
+    csrk_batch* b = new (std::nothrow) csrk_batch();
+    if (!b) return fail(CSRK_ERR_ALLOC, "out of host memory");
+    int rc = CSRK_OK;
+    try {
+        b->nmat = count;
+        b->hs.assign(hs, hs + count);
+        b->k.assign(k, k + count);
+        int dev = 0;
+        cudaGetDevice(&dev);
+        b->device = dev;
+        cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, dev);
+        std::vector<BatchTile> tiles;
+        std::vector<double> weight;
+        std::vector<Chunk> chunks;
+        std::vector<int32_t> sys_mat, sys_col, sys_off(count), mc0(count), mc1(count);
+        std::vector<int64_t> moff(count), mlen(count);
+        int64_t off = 0;
+        for (int32_t i = 0; i < count && !rc; ++i) {
+            csrk_matrix* h = hs[i];
+            if (!h || !h->have_ptrs) { rc = fail(CSRK_ERR_STATE, "every batch matrix needs its pointer arrays"); break; }
+            if (k[i] < 1 || k[i] > 64) { rc = fail(CSRK_ERR_ARG, "k must be in [1, 64]"); break; }
+            if ((rc = ensure_context(h)) || (rc = ensure_struct(h)) || (rc = ensure_vals(h, (int)h->dtype))) break;
+            if (h->device != dev) { rc = fail(CSRK_ERR_STATE, "batch matrices must live on the current device"); break; }
+            BatchMat m{};
+            m.rowptr = h->d_rowptr;
+            m.colidx = h->d_colidx;
+            m.vals = h->d_vals[(int)h->dtype];
+            m.sr_ptr = h->d_sr_ptr;
+            m.desc = h->d_desc;
+            m.n = h->m.n;
+            m.k = k[i];
+            m.vt = (int)h->dtype;
+            b->h_mats.push_back(m);
+            // tiles of about 32K nonzeros (whole SSRs)
+            const int32_t nssr = (int32_t)h->desc.size();
+            int32_t t0 = 0;
+            int64_t acc = 0;
+            for (int32_t t = 0; t < nssr; ++t) {
+                acc += h->desc[t].p1 - h->desc[t].p0;
+                if (acc >= 32768 || t == nssr - 1) {
+                    tiles.push_back({i, t0, t + 1, 0});
+                    weight.push_back((double)acc * (k[i] == 1 ? 1.0 : 0.5 + 0.5 * k[i]));
+                    t0 = t + 1;
+                    acc = 0;
+                }
+            }
+            // vector chunks of about 8K elements (whole rows)
+            sys_off[i] = (int32_t)sys_mat.size();
+            for (int c = 0; c < k[i]; ++c) {
+                sys_mat.push_back(i);
+                sys_col.push_back(c);
+            }
+            mc0[i] = (int32_t)chunks.size();
+            const int32_t rows_per_chunk = std::max<int32_t>(1, 8192 / k[i]);
+            for (int32_t r0 = 0; r0 < m.n; r0 += rows_per_chunk)
+                chunks.push_back({i, r0, std::min(m.n, r0 + rows_per_chunk), 0, off + (int64_t)r0 * k[i]});
+            mc1[i] = (int32_t)chunks.size();
+            moff[i] = off;
+            mlen[i] = (int64_t)m.n * k[i];
+            off += mlen[i];
+        }
+        if (!rc) {
+            std::vector<size_t> order(tiles.size());
+            std::iota(order.begin(), order.end(), 0);
+            std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t c) { return weight[a] > weight[c]; });
+            std::vector<BatchTile> sorted;
+            for (size_t q : order) sorted.push_back(tiles[q]);
+            b->ntiles = (int32_t)sorted.size();
+            b->nchunks = (int32_t)chunks.size();
+            b->nsys = (int32_t)sys_mat.size();
+            b->total = off;
+            if (!rc) rc = upload(&b->d_tiles, sorted);
+            if (!rc) rc = upload(&b->d_chunks, chunks);
+            if (!rc) rc = upload(&b->d_sys_mat, sys_mat);
+            if (!rc) rc = upload(&b->d_sys_col, sys_col);
+            if (!rc) rc = upload(&b->d_sys_off, sys_off);
+            if (!rc) rc = upload(&b->d_mat_chunk0, mc0);
+            if (!rc) rc = upload(&b->d_mat_chunk1, mc1);
+            if (!rc) rc = upload(&b->d_moff, moff);
+            if (!rc) rc = upload(&b->d_mlen, mlen);
+            if (!rc) rc = dmalloc(&b->d_mats_user, count);
+            if (!rc) rc = dmalloc(&b->d_mats_pq, count);
+            if (!rc) rc = dmalloc(&b->d_mats_xr, count);
+            if (!rc) rc = dmalloc(&b->d_counters, 2);
+            if (!rc && cudaMemset(b->d_counters, 0, 2 * sizeof(uint32_t)) != cudaSuccess)
+                rc = fail(CSRK_ERR_CUDA, "batch counters");
+            if (!rc && cudaMallocHost(&b->h_pinned_mats, count * sizeof(BatchMat)) != cudaSuccess)
+                rc = fail(CSRK_ERR_ALLOC, "batch pinned table");
+        }
+    } catch (const std::bad_alloc&) {
+        rc = fail(CSRK_ERR_ALLOC, "out of host memory");
+    }
+    if (rc) {
+        batch_free(b);
+        delete b;
+        return rc;
+    }
+    *out = b;
+    return CSRK_OK;
+}
+
+int csrk_batch_spmm(csrk_batch_handle b, double alpha, const void* const* X, double beta,
+                    void* const* Y, unsigned flags, void* stream) {
+    if (!b || !X || !Y) return fail(CSRK_ERR_ARG, "NULL argument");
+    if (!(flags & CSRK_VEC_PERMUTED) || (flags & ~CSRK_VEC_PERMUTED))
+        return fail(CSRK_ERR_UNSUPPORTED, "batched calls take FP64 vectors in the reordered numbering "
+                                          "(flags = CSRK_VEC_PERMUTED)");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // re-bind the vectors only when they changed (the table lives on the device)
+    bool same = b->bound_x.size() == (size_t)b->nmat;
+    for (int32_t i = 0; same && i < b->nmat; ++i) same = b->bound_x[i] == X[i] && b->bound_y[i] == Y[i];
+    if (!same) {
+        // the pinned staging table may still feed an earlier copy: wait for it first
+        CK_CUDA(cudaStreamSynchronize(s), "synchronise");
+        for (int32_t i = 0; i < b->nmat; ++i) {
+            if (!X[i] || !Y[i] || X[i] == Y[i]) return fail(CSRK_ERR_ARG, "bad vector pointer");
+            b->h_pinned_mats[i] = b->h_mats[i];
+            b->h_pinned_mats[i].X = static_cast<const double*>(X[i]);
+            b->h_pinned_mats[i].Y = static_cast<double*>(Y[i]);
+        }
+        CK_CUDA(cudaMemcpyAsync(b->d_mats_user, b->h_pinned_mats, b->nmat * sizeof(BatchMat),
+                                cudaMemcpyHostToDevice, s), "bind vectors");
+        b->bound_x.assign(X, X + b->nmat);
+        b->bound_y.assign(Y, Y + b->nmat);
+    }
+    return launch_batch_spmm(b, b->d_mats_user, alpha, beta, s);
+}
+
+static int bcg_enqueue_iteration(csrk_batch* b, cudaStream_t s) {
+    const int gv = b->nchunks;
+    const int fin_blocks = (b->nsys * 32 + 255) / 256;
+    int rc;
+    if ((rc = launch_batch_spmm(b, b->d_mats_pq, 1.0, 0.0, s))) return rc;   // Q = A P
+    bcg_dot<<<gv, VT_THREADS, 0, s>>>(b->d_chunks, b->d_mats_pq, b->P, b->Q, b->partials);
+    bcg_finalize<<<fin_blocks, 256, 0, s>>>(b->d_sys_mat, b->d_sys_col, b->d_mat_chunk0, b->d_mat_chunk1,
+                                            b->partials, b->st, b->nsys, 1, 0.0, nullptr);
+    bcg_update_xr<<<gv, VT_THREADS, 0, s>>>(b->d_chunks, b->d_mats_pq, b->d_sys_off, b->st, b->X, b->R, b->P,
+                                            b->Q, b->partials);
+    bcg_finalize<<<fin_blocks, 256, 0, s>>>(b->d_sys_mat, b->d_sys_col, b->d_mat_chunk0, b->d_mat_chunk1,
+                                            b->partials, b->st, b->nsys, 2, 0.0, nullptr);
+    bcg_update_p<<<gv, VT_THREADS, 0, s>>>(b->d_chunks, b->d_mats_pq, b->d_sys_off, b->st, b->R, b->P);
+    CK_CUDA(cudaGetLastError(), "batched CG launch");
+    return CSRK_OK;
+}
+
+int csrk_batch_cg(csrk_batch_handle b, const double* const* B, double* const* Xout, int32_t iters,
+                  double rtol, double* relres, int32_t* iters_done, void* stream) {
+    if (!b || !B || !Xout || iters < 1 || !(rtol >= 0.0)) return fail(CSRK_ERR_ARG, "bad batched CG arguments");
+    for (int32_t i = 0; i < b->nmat; ++i) {
+        const int k = b->k[i];
+        if (k & (k - 1) || k > 32) return fail(CSRK_ERR_UNSUPPORTED, "batched CG takes k in {1,2,4,8,16,32}");
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int rc;
+    if (!b->B) {
+        const size_t tot = (size_t)b->total;
+        if ((rc = dmalloc(&b->B, tot)) || (rc = dmalloc(&b->X, tot)) || (rc = dmalloc(&b->R, tot)) ||
+            (rc = dmalloc(&b->P, tot)) || (rc = dmalloc(&b->Q, tot)) ||
+            (rc = dmalloc(&b->partials, (size_t)b->nchunks * 32)) || (rc = dmalloc(&b->st, (size_t)b->nsys)) ||
+            (rc = dmalloc(&b->d_true, (size_t)b->nsys)) || (rc = dmalloc(&b->d_ptrs_in, (size_t)b->nmat)) ||
+            (rc = dmalloc(&b->d_ptrs_out, (size_t)b->nmat)))
+            return rc;
+        if ((rc = fill_table(b, b->d_mats_pq, b->P, b->Q)) || (rc = fill_table(b, b->d_mats_xr, b->X, b->R)))
+            return rc;
+        CK_CUDA(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking), "batch stream");
+    }
+    CK_CUDA(cudaMemcpyAsync(b->d_ptrs_in, B, b->nmat * sizeof(double*), cudaMemcpyHostToDevice, s), "B pointers");
+    CK_CUDA(cudaMemcpyAsync(b->d_ptrs_out, Xout, b->nmat * sizeof(double*), cudaMemcpyHostToDevice, s), "X pointers");
+    const dim3 cg_grid(64, std::min<int32_t>(b->nmat, 65535));
+    bcg_gather<<<cg_grid, 256, 0, s>>>(b->d_ptrs_in, b->d_moff, b->d_mlen, b->nmat, b->B);
+    const int fin_blocks = (b->nsys * 32 + 255) / 256;
+    bcg_init<<<b->nchunks, VT_THREADS, 0, s>>>(b->d_chunks, b->d_mats_pq, b->B, b->X, b->R, b->P, b->partials);
+    bcg_finalize<<<fin_blocks, 256, 0, s>>>(b->d_sys_mat, b->d_sys_col, b->d_mat_chunk0, b->d_mat_chunk1,
+                                            b->partials, b->st, b->nsys, 0, rtol, nullptr);
+    CK_CUDA(cudaGetLastError(), "batched CG init");
+    if (!b->exec || b->exec_iters != iters) {
+        if (b->exec) {
+            cudaGraphExecDestroy(b->exec);
+            b->exec = nullptr;
+        }
+        CK_CUDA(cudaStreamSynchronize(s), "synchronise");
+        CK_CUDA(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
+        for (int32_t it = 0; it < iters && !rc; ++it) rc = bcg_enqueue_iteration(b, b->cap);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(b->cap, &graph);
+        if (rc) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "end capture");
+        e = cudaGraphInstantiate(&b->exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
+        b->exec_iters = iters;
+    }
+    CK_CUDA(cudaGraphLaunch(b->exec, s), "graph launch");
+    // true residuals: R = B - A X, then per-system norms
+    CK_CUDA(cudaMemcpyAsync(b->R, b->B, (size_t)b->total * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy B");
+    if ((rc = launch_batch_spmm(b, b->d_mats_xr, -1.0, 1.0, s))) return rc;   // R = B - A X
+    bcg_dot<<<b->nchunks, VT_THREADS, 0, s>>>(b->d_chunks, b->d_mats_pq, b->R, b->R, b->partials);
+    bcg_finalize<<<fin_blocks, 256, 0, s>>>(b->d_sys_mat, b->d_sys_col, b->d_mat_chunk0, b->d_mat_chunk1,
+                                            b->partials, b->st, b->nsys, 3, 0.0, b->d_true);
+    bcg_scatter<<<cg_grid, 256, 0, s>>>(b->X, b->d_moff, b->d_mlen, b->nmat, b->d_ptrs_out);
+    CK_CUDA(cudaGetLastError(), "batched CG finish");
+    std::vector<SysState> hs(b->nsys);
+    CK_CUDA(cudaMemcpyAsync(hs.data(), b->st, b->nsys * sizeof(SysState), cudaMemcpyDeviceToHost, s), "read state");
+    if (relres)
+        CK_CUDA(cudaMemcpyAsync(relres, b->d_true, b->nsys * sizeof(double), cudaMemcpyDeviceToHost, s), "read relres");
+    CK_CUDA(cudaStreamSynchronize(s), "synchronise");
+    if (iters_done)
+        for (int32_t q = 0; q < b->nsys; ++q) iters_done[q] = hs[q].iters;
+    return CSRK_OK;
+}
+
+int csrk_batch_destroy(csrk_batch_handle b) {
+    if (!b) return CSRK_OK;
+    cudaDeviceSynchronize();
+    batch_free(b);
+    delete b;
+    return CSRK_OK;
+}
+
+int csrk_batch_info(csrk_batch_handle b, int32_t* nmat, int32_t* nsys, int32_t* ntiles, int64_t* total) {
+    if (!b) return fail(CSRK_ERR_ARG, "NULL batch");
+    if (nmat) *nmat = b->nmat;
+    if (nsys) *nsys = b->nsys;
+    if (ntiles) *ntiles = b->ntiles;
+    if (total) *total = b->total;
+    return CSRK_OK;
+}
+
+}  // extern "C"

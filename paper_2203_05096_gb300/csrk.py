@@ -57,6 +57,11 @@ _PROTOS = {
     "csrk_set_config": [_vp, _i32, _i32, _i32, _i32, _i32, _i32],
     "csrk_device_status": [_vp, _vp, _pi32],
     "csrk_cg": [_vp, _vp, _vp, _d, _i32, ctypes.c_int, _i32, _i32, _u, _pi32, ctypes.POINTER(_d), _vp],
+    "csrk_batch_create": [_vp, _i32, _vp, ctypes.POINTER(_vp)],
+    "csrk_batch_spmm": [_vp, _d, _vp, _d, _vp, _u, _vp],
+    "csrk_batch_cg": [_vp, _vp, _vp, _i32, _d, _vp, _vp, _vp],
+    "csrk_batch_info": [_vp, _pi32, _pi32, _pi32, _pi64],
+    "csrk_batch_destroy": [_vp],
     "csrk_spmv_static_scratch": [_i32, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _d, _vp, _d, _vp, _vp],
 }
 
@@ -234,6 +239,46 @@ def cg(h, b, x, rtol=1e-10, maxit=10000, inner="f64", replace_every=20, restart=
     if check and rc not in (0, 8):
         _check(rc, "csrk_cg")
     return rc, it.value, rel.value
+
+
+def batch_create(handles, ks):
+    hs = (_vp * len(handles))(*handles)
+    k, pk = _host(ks, np.int32)
+    out = _vp()
+    _check(lib().csrk_batch_create(hs, len(handles), pk, ctypes.byref(out)), "csrk_batch_create")
+    return out.value
+
+
+def _ptr_array(ts):
+    return (_vp * len(ts))(*[_ptr(t) for t in ts])
+
+
+def batch_spmm(b, alpha, Xs, beta, Ys, flags=VEC_PERMUTED, stream=None):
+    _check(lib().csrk_batch_spmm(b, float(alpha), _ptr_array(Xs), float(beta), _ptr_array(Ys), int(flags),
+                                 _stream(stream, *Xs)), "csrk_batch_spmm")
+
+
+def batch_info(b):
+    v = [ctypes.c_int32() for _ in range(3)]
+    t = ctypes.c_int64()
+    _check(lib().csrk_batch_info(b, *[ctypes.byref(x) for x in v], ctypes.byref(t)), "csrk_batch_info")
+    return dict(nmat=v[0].value, nsys=v[1].value, ntiles=v[2].value, total=t.value)
+
+
+def batch_cg(b, Bs, Xs, iters, rtol=1e-10, stream=None):
+    """Returns (relres per system, iterations per system)."""
+    nsys = batch_info(b)["nsys"]
+    rel = np.empty(nsys, np.float64)
+    its = np.empty(nsys, np.int32)
+    _check(lib().csrk_batch_cg(b, _ptr_array(Bs), _ptr_array(Xs), int(iters), float(rtol),
+                               rel.ctypes.data_as(_vp), its.ctypes.data_as(_vp), _stream(stream, *Bs)),
+           "csrk_batch_cg")
+    return rel, its
+
+
+def batch_destroy(b):
+    if b:
+        _check(lib().csrk_batch_destroy(b), "csrk_batch_destroy")
 
 
 def spmv_static_scratch(n, nssr, ssr_ptr, sr_ptr, rowptr, colidx, vals, perm, alpha, x, beta, y,

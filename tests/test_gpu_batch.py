@@ -1,0 +1,124 @@
+"""Batched persistent SpMM and batched CG over matrices of uneven size, against the oracle."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import precision
+from oracle import spmv as ospmv
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2203_05096_gb300 import csrk  # noqa: E402
+
+DEV = "cuda:0"
+
+
+def narrowed(vals, dtype):
+    if dtype == "f64":
+        return vals
+    if dtype == "f32":
+        return precision.to_f32(vals).astype(np.float64)
+    return precision.bf16_bits_to_f64(precision.to_bf16_bits(vals))
+
+
+def make_batch(specs):
+    """specs: list of (CSR, dtype, k, (sr, ssr)); returns handles, exported reordered CSRs."""
+    hs, forms = [], []
+    for a, dtype, k, sizes in specs:
+        h = csrk.create(a.n, a.rowptr, a.colidx, a.vals, dtype)
+        csrk.reorder(h)
+        csrk.set_sizes(h, *sizes)
+        e = csrk.export(h)
+        forms.append((e["rowptr"], e["colidx"], narrowed(e["vals"], dtype)))
+        hs.append(h)
+    return hs, forms
+
+
+SPECS = [
+    (synth.stencil_3d(17, 13, 11, 27, "random_dd", 1), "f64", 1, (32, 4)),
+    (synth.stencil_3d(23, 19, 7, 7, "random_dd", 2), "f32", 2, (16, 8)),
+    (synth.fem_like(9, 3), "f64", 3, (32, 2)),
+    (synth.stencil_3d(5, 5, 5, 27, "random_dd", 4), "bf16", 4, (8, 3)),
+    (synth.random_pattern(333, 0.02, 5, symmetric=True, empty_rows=11), "f64", 8, (32, 8)),
+    (synth.stencil_3d(31, 29, 3, 7, "random_dd", 6), "f64", 16, (64, 2)),
+    (synth.stencil_2d_5pt(20, 9), "f32", 33, (32, 1)),
+]
+
+
+def test_batch_spmm_matches_oracle_and_replays():
+    hs, forms = make_batch(SPECS)
+    ks = [k for _, _, k, _ in SPECS]
+    b = csrk.batch_create(hs, ks)
+    info = csrk.batch_info(b)
+    assert info["nmat"] == len(SPECS) and info["nsys"] == sum(ks)
+    Xs, Ys, Y0s = [], [], []
+    for i, (a, _, k, _) in enumerate(SPECS):
+        X = synth.uniform_block(a.n, k, 100 + i)
+        Y0 = synth.uniform_block(a.n, k, 200 + i)
+        Xs.append(torch.tensor(X, device=DEV))
+        Ys.append(torch.tensor(Y0, device=DEV))
+        Y0s.append(Y0)
+    for rep in range(3):                        # the tile counter resets itself between launches
+        for i in range(len(SPECS)):
+            Ys[i].copy_(torch.tensor(Y0s[i], device=DEV))
+        csrk.batch_spmm(b, 1.5, Xs, -0.5, Ys)
+        torch.cuda.synchronize()
+        for i, ((a, _, k, _), (rp, ci, v)) in enumerate(zip(SPECS, forms)):
+            X = Xs[i].cpu().numpy()
+            ref = ospmv.csr_spmm(a.n, rp, ci, v, X, 1.5, -0.5, Y0s[i])
+            got = Ys[i].cpu().numpy()
+            for c in range(k):
+                s = ospmv.abs_row_scale(rp, ci, v, X[:, c], 1.5, -0.5, Y0s[i][:, c])
+                assert np.all(np.abs(got[:, c] - ref[:, c]) <= 1e-12 * s), (i, c, rep)
+    # new output buffers: the bound table is rebuilt
+    Zs = [torch.zeros_like(y) for y in Ys]
+    csrk.batch_spmm(b, 1.0, Xs, 0.0, Zs)
+    torch.cuda.synchronize()
+    (rp, ci, v), (a, _, k, _) = forms[0], SPECS[0]
+    ref = ospmv.csr_spmm(a.n, rp, ci, v, Xs[0].cpu().numpy())
+    assert np.allclose(Zs[0].cpu().numpy(), ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+    csrk.batch_destroy(b)
+    for h in hs:
+        csrk.destroy(h)
+
+
+def test_batch_cg_converges_per_system():
+    specs = [(synth.stencil_3d(14, 13, 12, 27, "random_dd", 7), "f64", 4, (32, 4)),
+             (synth.stencil_3d(20, 20, 9, 7, "random_dd", 8), "f64", 1, (32, 8)),
+             (synth.fem_like(8, 9), "f32", 2, (32, 2)),
+             (synth.stencil_3d(6, 6, 6, 27, "random_dd", 10), "f64", 16, (16, 4))]
+    hs, forms = make_batch(specs)
+    b = csrk.batch_create(hs, [k for _, _, k, _ in specs])
+    Bs = [torch.tensor(synth.uniform_block(a.n, k, 300 + i), device=DEV) for i, (a, _, k, _) in enumerate(specs)]
+    Xs = [torch.zeros_like(x) for x in Bs]
+    rel, its = csrk.batch_cg(b, Bs, Xs, 200, 1e-10)
+    assert np.all(rel <= 1.05e-10), rel
+    assert np.all(its > 0) and np.all(its <= 200)
+    q = 0
+    for i, ((a, _, k, _), (rp, ci, v)) in enumerate(zip(specs, forms)):
+        X, B = Xs[i].cpu().numpy(), Bs[i].cpu().numpy()
+        for c in range(k):
+            r = B[:, c] - ospmv.csr_spmv(a.n, rp, ci, v, X[:, c])
+            true = np.linalg.norm(r) / np.linalg.norm(B[:, c])
+            assert true <= 1.05e-10 and abs(true - rel[q]) <= 1e-12 + 1e-3 * true
+            q += 1
+    # a second solve replays the same graph
+    rel2, its2 = csrk.batch_cg(b, Bs, Xs, 200, 1e-10)
+    assert np.array_equal(its, its2) and np.allclose(rel, rel2, rtol=1e-12, atol=0)
+    csrk.batch_destroy(b)
+    for h in hs:
+        csrk.destroy(h)
+
+
+def test_batch_rejects_natural_numbering():
+    a = synth.stencil_2d_5pt(8, 8)
+    h = csrk.create(a.n, a.rowptr, a.colidx, a.vals)
+    csrk.set_sizes(h, 8, 2)
+    b = csrk.batch_create([h], [1])
+    x = torch.zeros(a.n, dtype=torch.float64, device=DEV)
+    with pytest.raises(csrk.CsrkError) as ei:
+        csrk.batch_spmm(b, 1.0, [x], 0.0, [torch.zeros_like(x)], flags=0)
+    assert ei.value.status == "ERR_UNSUPPORTED"
+    csrk.batch_destroy(b)
+    csrk.destroy(h)
