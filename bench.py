@@ -71,6 +71,21 @@ def dist_env():
     return world, rank, local
 
 
+def max_over_ranks(ms, dist=None, device="cpu"):
+    """Slowest rank's time (the job is done when the last replica is); `dist` may be None."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(ms)
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, units_per_rank, ms):
+    """Units all replicas processed per second, over the slowest replica's time."""
+    return world * units_per_rank / (ms * 1e-3)
+
+
 def build_matrices(side=SIDE, only=None):
     n = side ** 3
     labels = synth.vectors.permutation(n, 3)
@@ -253,16 +268,13 @@ def run_ours(args, world, rank, local):
         dist.barrier()
     ms = t_start.elapsed_time(t_end)
     kern_ms = [[events[j][0][i].elapsed_time(events[j][1][i]) for i in range(K)] for j in range(len(state))]
-    if dist is not None:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, dev)
     status = sum(csrk.device_status(s["h"]) for s in state)
     if status:
         raise RuntimeError("device status word set during the timed region")
 
     flops_step = sum(2.0 * s["a"].nnz for s in state)
-    value = world * K * flops_step / (ms * 1e-3) / 1e9
+    value = whole_job_rate(world, K * flops_step, ms) / 1e9
 
     # roofline of the dominant kernel: the 27-point CSR-3 launch
     peak, peak_kind = measured_peaks()
@@ -313,12 +325,8 @@ def run_ours(args, world, rank, local):
             e2e_step()
         e1.record(stream)
         torch.cuda.synchronize()
-        ems = e0.elapsed_time(e1)
-        if dist is not None:
-            t = torch.tensor([ems], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems = float(t.item())
-        e2e = {"value": round(world * E * flops_step / (ems * 1e-3) / 1e9, 2), "unit": "GFLOP/s",
+        ems = max_over_ranks(e0.elapsed_time(e1), dist, dev)
+        e2e = {"value": round(whole_job_rate(world, E * flops_step, ems) / 1e9, 2), "unit": "GFLOP/s",
                "h2d_bytes_per_step": int(sum(8 * s["a"].n for s in state)),
                "d2h_bytes_per_step": int(sum(8 * s["a"].n for s in state))}
 
@@ -346,6 +354,10 @@ def run_ours(args, world, rank, local):
         f64 = cg["runs"]["f64"]["ms"]
         for k in ("f32", "bf16"):
             cg["runs"][k]["speedup_vs_f64"] = round(f64 / cg["runs"][k]["ms"], 3)
+
+    batch = None
+    if not args.no_batch:
+        batch = run_batch(args, dev, stream, peak)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -379,6 +391,7 @@ def run_ours(args, world, rank, local):
                          "kernel_hash": khash},
             "e2e": e2e,
             "cg": cg,
+            "batch": batch,
             "gpu_launches": K * 3 * len(state),
             "clocks": clocks,
             "cpu_baseline": cpu,
@@ -389,6 +402,64 @@ def run_ours(args, world, rank, local):
         csrk.destroy(s["h"])
     if dist is not None:
         dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------ batched workload
+def run_batch(args, dev, stream, peak):
+    """64 stencil / FEM matrices, n log-uniform in [1e3, 1e6] (seed 6), FP64 and FP32 values,
+    k in {1,2,4,8,16} right-hand sides; sizes from the autotuner; one persistent SpMM
+    launch per step, then 200 CG iterations recorded in one CUDA graph."""
+    import torch
+    from paper_2203_05096_gb300 import csrk
+    specs = synth.batch_specs()
+    t0 = time.perf_counter()
+    hs, mats = [], []
+    for sp in specs:
+        a = synth.batch_matrix(sp)
+        h = csrk.create(a.n, a.rowptr, a.colidx, a.vals, sp["dtype"])
+        csrk.reorder(h, "rcm", want_perm=False)
+        csrk.set_sizes(h, 0, 0)
+        hs.append(h)
+        mats.append((a.n, a.nnz, sp))
+    setup_s = time.perf_counter() - t0
+    ks = [sp["k"] for sp in specs]
+    b = csrk.batch_create(hs, ks)
+    Xs = [torch.tensor(synth.uniform_block(n, sp["k"], 500 + i), device=dev) for i, (n, _, sp) in enumerate(mats)]
+    Ys = [torch.empty_like(x) for x in Xs]
+    for _ in range(3):
+        csrk.batch_spmm(b, 1.0, Xs, 0.0, Ys)
+    torch.cuda.synchronize()
+    reps = 20
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        csrk.batch_spmm(b, 1.0, Xs, 0.0, Ys)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    flops = sum(2.0 * nnz * sp["k"] for (n, nnz, sp) in mats)
+    vbytes = sum(({"f64": 8, "f32": 4}[sp["dtype"]] + 4) * nnz + 4 * (n + 1) + 16 * n * sp["k"]
+                 for (n, nnz, sp) in mats)
+    out = {"matrices": len(mats), "n_total": int(sum(m[0] for m in mats)),
+           "nnz_total": int(sum(m[1] for m in mats)), "systems": int(sum(ks)), "setup_s": round(setup_s, 1),
+           "spmm_ms": round(ms, 4), "spmm_gflops": round(flops / (ms * 1e-3) / 1e9, 1),
+           "spmm_gbs": round(vbytes / (ms * 1e-3) / 1e9, 1),
+           "spmm_frac_of_peak": round(vbytes / (ms * 1e-3) / 1e9 / peak, 3), "launches_per_step": 1}
+    Bs = [torch.tensor(synth.uniform_block(n, sp["k"], 700 + i), device=dev) for i, (n, _, sp) in enumerate(mats)]
+    Xc = [torch.zeros_like(x) for x in Bs]
+    csrk.batch_cg(b, Bs, Xc, 200, 1e-10)          # records the 200-iteration graph
+    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    c0.record(stream)
+    rel, its = csrk.batch_cg(b, Bs, Xc, 200, 1e-10)
+    c1.record(stream)
+    torch.cuda.synchronize()
+    out["cg"] = {"iterations_in_graph": 200, "ms": round(c0.elapsed_time(c1), 3),
+                 "converged_systems": int(np.sum(rel <= 1e-10)), "max_relres": float(np.max(rel)),
+                 "median_iterations": float(np.median(its))}
+    csrk.batch_destroy(b)
+    for h in hs:
+        csrk.destroy(h)
+    return out
 
 
 # ------------------------------------------------------------------ reference arm
@@ -461,6 +532,7 @@ def main():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cg", action="store_true")
+    p.add_argument("--no-batch", action="store_true")
     p.add_argument("--side", type=int, default=SIDE, help="grid side (profiling runs use a smaller case)")
     p.add_argument("--only", choices=[m for m, _ in MATRICES], default=None)
     args = p.parse_args()

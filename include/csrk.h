@@ -197,7 +197,8 @@ int csrk_cg(csrk_handle h, const double* b, double* x, double rtol, int32_t maxi
  *   hs     count handles, each with its pointer arrays set (sizes or explicit); any
  *          value dtype; all on the current device
  *   k      right-hand sides per matrix, 1..64
- * Tiles of about 32K nonzeros (whole super-super-rows) are sorted by decreasing work.
+ * Tiles of about 32K nonzeros (whole super-super-rows) are queued matrix by matrix
+ * (matrices by decreasing work, each matrix's tiles in row order).
  * Uploads the handles' device forms if needed.  Errors: CSRK_ERR_ARG, CSRK_ERR_STATE,
  * CSRK_ERR_ALLOC, CSRK_ERR_CUDA. */
 int csrk_batch_create(const csrk_handle* hs, int32_t count, const int32_t* k,
@@ -324,6 +325,15 @@ int csrk_spmv_static_scratch(int32_t n, int32_t nssr, const int32_t* ssr_ptr,
                              const int32_t* colidx, const double* vals, const int32_t* perm,
                              double alpha, const double* x, double beta, double* y,
                              void* stream);
+
+/* csrk_selftest_bounded_wait: check the device-side timeout path.  Launches one block
+ * that waits, with the same bounded wait the CSR-3 kernel uses, on an mbarrier that
+ * nothing completes; the wait gives up after timeout_ns (at most 10 s), sets the handle's
+ * status word and the kernel returns, leaving the context usable.  Synchronises `stream`
+ * and returns the status read (and cleared) as csrk_device_status does: CSRK_ERR_TIMEOUT
+ * with *status = 1 is the expected outcome. */
+int csrk_selftest_bounded_wait(csrk_handle h, uint64_t timeout_ns, void* stream,
+                               int32_t* status);
 
 const char* csrk_last_error(void);
 

@@ -878,6 +878,16 @@ int csrk_device_status(csrk_handle h, void* stream, int32_t* status) {
     return CSRK_OK;
 }
 
+int csrk_selftest_bounded_wait(csrk_handle h, uint64_t timeout_ns, void* stream, int32_t* status) {
+    if (!h || !status || timeout_ns == 0 || timeout_ns > 10000000000ull)
+        return fail(CSRK_ERR_ARG, "bad arguments (timeout_ns in (0, 1e10])");
+    int rc;
+    if ((rc = ensure_context(h))) return rc;
+    const int e = launch_bounded_wait_probe(timeout_ns, h->d_status, stream);
+    if (e) return cuda_fail((cudaError_t)e, "probe launch");
+    return csrk_device_status(h, stream, status);
+}
+
 const char* csrk_last_error(void) { return g_last_error.c_str(); }
 
 const char* csrk_build_info(void) {

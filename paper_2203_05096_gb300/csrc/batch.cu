@@ -2,7 +2,8 @@
 //
 // csrk_batch_spmm: Y_i = alpha A_i X_i + beta Y_i for every matrix i of a batch in ONE
 // persistent launch.  The work list holds tiles (matrix, range of super-super-rows),
-// sorted by decreasing work; each thread block takes the next tile with an atomic counter
+// matrices by decreasing work and each matrix's tiles in row order (neighbouring blocks
+// share the matrix's x window in L2); each thread block takes the next tile with an atomic counter
 // (no block ever waits for another) and runs the tile's super-rows on its warps, with the
 // row mapping of the matrix's right-hand-side count (one row per lane for k = 1, k lanes
 // per row otherwise).  The last block to finish resets the counter, so the launch can be
@@ -50,36 +51,35 @@ struct Chunk {   // contiguous rows of one matrix for the batched vector kernels
 
 constexpr int BW = 8;   // warps per block of the persistent SpMM
 
-template <typename VT>
-__device__ __forceinline__ void tile_rows(const BatchMat& m, int rb, int re, double alpha, double beta,
-                                          int epi, int lane) {
-    const VT* vals = static_cast<const VT*>(m.vals);
+// One super-row of a batch matrix, for one (value type, right-hand-side count) class.  Kept
+// out of line: each class gets its own register allocation instead of one kernel body
+// holding every variant at once.
+template <typename VT, int G, int CPL>
+__device__ __noinline__ void sr_rows(const BatchMat* m, int rb, int re, double alpha, double beta, int epi,
+                                     int lane) {
     using namespace csrk::dev;
-    switch (m.k) {
-        case 1:
-            spmv_rows<VT, double, double, 1, 8>(rb, re, m.rowptr, m.colidx, vals, m.X, m.Y, alpha, beta, epi, lane);
-            break;
-        case 2:
-            spmm_rows<VT, double, double, 2, 1>(rb, re, m.rowptr, m.colidx, vals, m.X, 2, m.Y, 2, 2, alpha, beta, epi, lane);
-            break;
-        case 3:
-        case 4:
-            spmm_rows<VT, double, double, 4, 1>(rb, re, m.rowptr, m.colidx, vals, m.X, m.k, m.Y, m.k, m.k, alpha, beta, epi, lane);
-            break;
-        case 5: case 6: case 7: case 8:
-            spmm_rows<VT, double, double, 8, 1>(rb, re, m.rowptr, m.colidx, vals, m.X, m.k, m.Y, m.k, m.k, alpha, beta, epi, lane);
-            break;
-        default:
-            if (m.k <= 16)
-                spmm_rows<VT, double, double, 16, 1>(rb, re, m.rowptr, m.colidx, vals, m.X, m.k, m.Y, m.k, m.k, alpha, beta, epi, lane);
-            else if (m.k <= 32)
-                spmm_rows<VT, double, double, 32, 1>(rb, re, m.rowptr, m.colidx, vals, m.X, m.k, m.Y, m.k, m.k, alpha, beta, epi, lane);
-            else
-                spmm_rows<VT, double, double, 32, 2>(rb, re, m.rowptr, m.colidx, vals, m.X, m.k, m.Y, m.k, m.k, alpha, beta, epi, lane);
-    }
+    const VT* vals = static_cast<const VT*>(m->vals);
+    if constexpr (G == 1)
+        spmv_rows<VT, double, double, 1, 8>(rb, re, m->rowptr, m->colidx, vals, m->X, m->Y, alpha, beta, epi, lane);
+    else
+        spmm_rows<VT, double, double, G, CPL>(rb, re, m->rowptr, m->colidx, vals, m->X, m->k, m->Y, m->k, m->k,
+                                              alpha, beta, epi, lane);
 }
 
-__global__ void __launch_bounds__(BW * 32) batch_spmm_kernel(const BatchMat* __restrict__ mats,
+template <typename VT>
+__device__ __forceinline__ void tile_rows(const BatchMat* m, int rb, int re, double alpha, double beta,
+                                          int epi, int lane) {
+    const int k = m->k;
+    if (k == 1) sr_rows<VT, 1, 1>(m, rb, re, alpha, beta, epi, lane);
+    else if (k == 2) sr_rows<VT, 2, 1>(m, rb, re, alpha, beta, epi, lane);
+    else if (k <= 4) sr_rows<VT, 4, 1>(m, rb, re, alpha, beta, epi, lane);
+    else if (k <= 8) sr_rows<VT, 8, 1>(m, rb, re, alpha, beta, epi, lane);
+    else if (k <= 16) sr_rows<VT, 16, 1>(m, rb, re, alpha, beta, epi, lane);
+    else if (k <= 32) sr_rows<VT, 32, 1>(m, rb, re, alpha, beta, epi, lane);
+    else sr_rows<VT, 32, 2>(m, rb, re, alpha, beta, epi, lane);
+}
+
+__global__ void __launch_bounds__(BW * 32, 4) batch_spmm_kernel(const BatchMat* __restrict__ mats,
                                                              const BatchTile* __restrict__ tiles,
                                                              int32_t ntiles, uint32_t* counters,
                                                              double alpha, double beta, int epi) {
@@ -92,16 +92,17 @@ __global__ void __launch_bounds__(BW * 32) batch_spmm_kernel(const BatchMat* __r
         __syncthreads();
         if (t >= ntiles) break;
         const BatchTile tl = tiles[t];
-        const BatchMat m = mats[tl.mat];
+        const BatchMat* m = &mats[tl.mat];
+        const SsrDesc* desc = m->desc;
+        const int32_t* sr_ptr = m->sr_ptr;
+        const int vt = m->vt;
         for (int32_t q = tl.t0; q < tl.t1; ++q) {
-            const SsrDesc d = m.desc[q];
+            const SsrDesc d = desc[q];
             for (int sr = d.s0 + warp; sr < d.s1; sr += BW) {
-                const int rb = m.sr_ptr[sr], re = m.sr_ptr[sr + 1];
-                switch (m.vt) {
-                    case csrk::VAL_F64: tile_rows<double>(m, rb, re, alpha, beta, epi, lane); break;
-                    case csrk::VAL_F32: tile_rows<float>(m, rb, re, alpha, beta, epi, lane); break;
-                    default: tile_rows<bf16_t>(m, rb, re, alpha, beta, epi, lane); break;
-                }
+                const int rb = sr_ptr[sr], re = sr_ptr[sr + 1];
+                if (vt == csrk::VAL_F64) tile_rows<double>(m, rb, re, alpha, beta, epi, lane);
+                else if (vt == csrk::VAL_F32) tile_rows<float>(m, rb, re, alpha, beta, epi, lane);
+                else tile_rows<bf16_t>(m, rb, re, alpha, beta, epi, lane);
             }
         }
     }
@@ -413,9 +414,22 @@ int csrk_batch_create(const csrk_handle* hs, int32_t count, const int32_t* k, cs
             off += mlen[i];
         }
         if (!rc) {
+            // Matrices in order of decreasing total work; within a matrix, tiles in SSR
+            // order, so the blocks running at any moment cover neighbouring rows of one
+            // matrix and share its x window in L2 (tiles sorted by work alone interleave
+            // many matrices and overflow L2 with their x windows).
+            std::vector<double> mwork(count, 0.0);
+            for (size_t q = 0; q < tiles.size(); ++q) mwork[tiles[q].mat] += weight[q];
             std::vector<size_t> order(tiles.size());
             std::iota(order.begin(), order.end(), 0);
-            std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t c) { return weight[a] > weight[c]; });
+            std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t c) {
+                if (tiles[a].mat != tiles[c].mat) {
+                    if (mwork[tiles[a].mat] != mwork[tiles[c].mat])
+                        return mwork[tiles[a].mat] > mwork[tiles[c].mat];
+                    return tiles[a].mat < tiles[c].mat;
+                }
+                return tiles[a].t0 < tiles[c].t0;
+            });
             std::vector<BatchTile> sorted;
             for (size_t q : order) sorted.push_back(tiles[q]);
             b->ntiles = (int32_t)sorted.size();

@@ -115,6 +115,7 @@ void set_last_error(const std::string& msg);
 // vec_kernels.cu
 int launch_gather_rows(const void* in, int64_t ldi, void* out, int64_t ldo, const int32_t* perm,
                        int32_t n, int32_t k, int elem_bytes, void* stream);
+int launch_bounded_wait_probe(unsigned long long timeout_ns, int32_t* status, void* stream);
 int launch_scatter_rows(const void* in, int64_t ldi, void* out, int64_t ldo, const int32_t* perm,
                         int32_t n, int32_t k, int elem_bytes, void* stream);
 

@@ -229,7 +229,9 @@ __device__ __forceinline__ void spmv_rows(int rb, int re, const int32_t* __restr
 }
 
 // SpMM pass: G lanes per row, lane c0 = lane % G owns columns c0, c0+G, ... (< k, CPL of
-// them).  X, Y row-major with leading dimensions ldx, ldy.
+// them).  X, Y row-major with leading dimensions ldx, ldy.  As in spmv_rows, the X gathers
+// of a chunk of 8 nonzeros are issued before their FMAs (a predicated 4-wide tail ends the
+// row), so each lane keeps several loads in flight.
 template <typename VT, typename XT, typename AT, int G, int CPL>
 __device__ __forceinline__ void spmm_rows(int rb, int re, const int32_t* __restrict__ rp,
                                           const int32_t* __restrict__ col_s,
@@ -238,29 +240,56 @@ __device__ __forceinline__ void spmm_rows(int rb, int re, const int32_t* __restr
                                           XT* __restrict__ Y, int64_t ldy, int k,
                                           double alpha, double beta, int epi, int lane) {
     constexpr int RPP = 32 / G;
+    constexpr int U = CPL == 1 ? 8 : 4;
     const int c0 = lane % G;
+    bool on[CPL];
+#pragma unroll
+    for (int j = 0; j < CPL; ++j) on[j] = c0 + j * G < k;
     for (int base = rb; base < re; base += RPP) {
         const int r = base + lane / G;
         if (r >= re) continue;
         AT acc[CPL];
 #pragma unroll
         for (int j = 0; j < CPL; ++j) acc[j] = 0;
-        const int pb = rp[r], pe = rp[r + 1];
-#pragma unroll 2
-        for (int p = pb; p < pe; ++p) {
-            const VT v = val_s[p];
-            const XT* xr = X + (int64_t)col_s[p] * ldx;
+        const int pe = rp[r + 1];
+        int p = rp[r];
+        for (; p + U <= pe; p += U) {
+            XT xv[U][CPL];
 #pragma unroll
-            for (int j = 0; j < CPL; ++j) {
-                const int c = c0 + j * G;
-                if (c < k) acc[j] = Acc<AT>::fma(v, ldg_x(&xr[c]), acc[j]);
+            for (int t = 0; t < U; ++t) {
+                const XT* xr = X + (int64_t)col_s[p + t] * ldx + c0;
+#pragma unroll
+                for (int j = 0; j < CPL; ++j) xv[t][j] = on[j] ? ldg_x(xr + j * G) : XT(0);
+            }
+#pragma unroll
+            for (int t = 0; t < U; ++t) {
+                const VT v = val_s[p + t];
+#pragma unroll
+                for (int j = 0; j < CPL; ++j) acc[j] = Acc<AT>::fma(v, xv[t][j], acc[j]);
+            }
+        }
+        for (; p < pe; p += 4) {
+            XT xv[4][CPL];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                if (p + t < pe) {
+                    const XT* xr = X + (int64_t)col_s[p + t] * ldx + c0;
+#pragma unroll
+                    for (int j = 0; j < CPL; ++j) xv[t][j] = on[j] ? ldg_x(xr + j * G) : XT(0);
+                }
+            }
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                if (p + t < pe) {
+                    const VT v = val_s[p + t];
+#pragma unroll
+                    for (int j = 0; j < CPL; ++j) acc[j] = Acc<AT>::fma(v, xv[t][j], acc[j]);
+                }
             }
         }
 #pragma unroll
-        for (int j = 0; j < CPL; ++j) {
-            const int c = c0 + j * G;
-            if (c < k) store_y<XT, AT>(Y + (int64_t)r * ldy, c, acc[j], alpha, beta, epi);
-        }
+        for (int j = 0; j < CPL; ++j)
+            if (on[j]) store_y<XT, AT>(Y + (int64_t)r * ldy, c0 + j * G, acc[j], alpha, beta, epi);
     }
 }
 

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include "csrk_internal.h"
+#include "kernels.cuh"
 
 namespace csrk {
 namespace {
@@ -65,6 +66,29 @@ int launch_scatter_rows(const void* in, int64_t ldi, void* out, int64_t ldo, con
         scatter_rows_kernel<double><<<grid, 256, 0, s>>>((const double*)in, ldi, (double*)out, ldo, perm, n, k);
     else
         scatter_rows_kernel<float><<<grid, 256, 0, s>>>((const float*)in, ldi, (float*)out, ldo, perm, n, k);
+    return (int)cudaGetLastError();
+}
+
+namespace {
+// One block: initialise an mbarrier that expects two arrivals, arrive once, and wait on
+// it with the kernels' bounded wait.  Nothing ever completes the phase, so the wait must
+// give up after timeout_ns and report through the status word.
+__global__ void bounded_wait_probe(unsigned long long timeout_ns, int32_t* status) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        dev::mbar_init(&bar, 2);
+        dev::fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        dev::mbar_arrive(&bar);
+        if (!dev::mbar_wait_bounded(&bar, 0, timeout_ns)) dev::report(status, 1);
+    }
+}
+}  // namespace
+
+int launch_bounded_wait_probe(unsigned long long timeout_ns, int32_t* status, void* stream) {
+    bounded_wait_probe<<<1, 32, 0, (cudaStream_t)stream>>>(timeout_ns, status);
     return (int)cudaGetLastError();
 }
 

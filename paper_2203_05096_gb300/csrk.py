@@ -57,6 +57,7 @@ _PROTOS = {
     "csrk_set_config": [_vp, _i32, _i32, _i32, _i32, _i32, _i32],
     "csrk_device_status": [_vp, _vp, _pi32],
     "csrk_cg": [_vp, _vp, _vp, _d, _i32, ctypes.c_int, _i32, _i32, _u, _pi32, ctypes.POINTER(_d), _vp],
+    "csrk_selftest_bounded_wait": [_vp, ctypes.c_uint64, _vp, _pi32],
     "csrk_batch_create": [_vp, _i32, _vp, ctypes.POINTER(_vp)],
     "csrk_batch_spmm": [_vp, _d, _vp, _d, _vp, _u, _vp],
     "csrk_batch_cg": [_vp, _vp, _vp, _i32, _d, _vp, _vp, _vp],
@@ -288,6 +289,13 @@ def spmv_static_scratch(n, nssr, ssr_ptr, sr_ptr, rowptr, colidx, vals, perm, al
                                           _ptr(rowptr), _ptr(colidx), _ptr(vals), _ptr(perm),
                                           float(alpha), _ptr(x), float(beta), _ptr(y),
                                           _stream(stream, x, y)), "csrk_spmv_static_scratch")
+
+
+def selftest_bounded_wait(h, timeout_ns=20_000_000, stream=None):
+    """Returns (status code, status word) of a wait that nothing completes."""
+    st = ctypes.c_int32()
+    rc = lib().csrk_selftest_bounded_wait(h, int(timeout_ns), _stream(stream), ctypes.byref(st))
+    return rc, st.value
 
 
 def build_info() -> str:
