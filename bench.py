@@ -4,10 +4,10 @@
 Workload (one "step"): y = A x on two 128^3 stencil matrices, 7-point (n = 2,097,152,
 nnz = 14,581,760) and 27-point (nnz = 55,742,968); FP64 values diagonally dominant with
 off-diagonals U[-1,0), int32 indices; the input rows/columns carry a random symmetric
-permutation (seed 3) that the CSR-k reorder (RCM) undoes; CSR-3 with super-rows of 32
-rows and super-super-rows of 8 super-rows; x ~ U[-1,1] (seed 2).  Each step runs, per
-matrix: permute x into the reordered numbering, the CSR-3 kernel, unpermute y -- the
-whole device path of a natural-numbering csrk_spmv call.  Inputs are resident in HBM
+permutation (seed 3) that the CSR-k reorder (RCM) undoes; CSR-3 sizes and launch shape
+from the library's autotuner; x ~ U[-1,1] (seed 2).  Each step runs, per matrix: permute
+x into the reordered numbering, then the CSR-3 kernel storing y in the input numbering
+(fused unpermute) -- the whole device path of a natural-numbering csrk_spmv call.  Inputs are resident in HBM
 and each step's working set (~930 MB) exceeds the 129 MB L2, so no flush is needed.
 
 Metric: GFLOP/s (2 flops per stored nonzero per SpMV), whole job over all ranks.
@@ -97,10 +97,12 @@ def build_matrices(side=SIDE, only=None):
     return out
 
 
-def alg_bytes_spmv(n, nnz, nsr, nssr, val_bytes=8, x_bytes=8):
+def alg_bytes_spmv(n, nnz, nsr, nssr, val_bytes=8, x_bytes=8, fused_unpermute=True):
     # every stored value and column index, rowptr, sr_ptr, the 32-byte SSR descriptors,
-    # x read once and y written once (beta = 0)
-    return (val_bytes + 4) * nnz + 4 * (n + 1) + 4 * (nsr + 1) + 32 * nssr + x_bytes * n + x_bytes * n
+    # x read once and y written once (beta = 0), and the permutation read once when the
+    # kernel stores y in the input numbering
+    return ((val_bytes + 4) * nnz + 4 * (n + 1) + 4 * (nsr + 1) + 32 * nssr + x_bytes * n + x_bytes * n
+            + (4 * n if fused_unpermute else 0))
 
 
 class ClockSampler:
@@ -218,18 +220,19 @@ def run_ours(args, world, rank, local):
                           cfg=csrk.tuned_config(h), tune_s=t_tune))
 
     perm_fn, spmv_fn = lib.csrk_permute, lib.csrk_spmv
-    VP = csrk.VEC_PERMUTED
+    XP = csrk.X_PERMUTED   # x in the reordered numbering, y stored to its input place
 
     def step(events=None, i=0):
         for j, s in enumerate(state):
             h = s["h"]
+            if events is not None:
+                events[j][2][i].record(stream)
             rc = perm_fn(h, 0, 1, s["x"].data_ptr(), 1, s["xp"].data_ptr(), 1, 0, sp)
             if events is not None:
                 events[j][0][i].record(stream)
-            rc |= spmv_fn(h, 1.0, s["xp"].data_ptr(), 0.0, s["yp"].data_ptr(), VP, sp)
+            rc |= spmv_fn(h, 1.0, s["xp"].data_ptr(), 0.0, s["y"].data_ptr(), XP, sp)
             if events is not None:
                 events[j][1][i].record(stream)
-            rc |= perm_fn(h, 1, 1, s["yp"].data_ptr(), 1, s["y"].data_ptr(), 1, 0, sp)
             if rc:
                 raise RuntimeError(lib.csrk_last_error().decode())
 
@@ -248,7 +251,7 @@ def run_ours(args, world, rank, local):
             raise RuntimeError(f"{s['name']}: result check failed before timing")
 
     K = args.steps
-    events = [[[torch.cuda.Event(enable_timing=True) for _ in range(K)] for _ in range(2)] for _ in state]
+    events = [[[torch.cuda.Event(enable_timing=True) for _ in range(K)] for _ in range(3)] for _ in state]
     t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     sampler = ClockSampler(visible_gpu_index(local))
     if dist is not None:
@@ -268,6 +271,7 @@ def run_ours(args, world, rank, local):
         dist.barrier()
     ms = t_start.elapsed_time(t_end)
     kern_ms = [[events[j][0][i].elapsed_time(events[j][1][i]) for i in range(K)] for j in range(len(state))]
+    perm_ms = [[events[j][2][i].elapsed_time(events[j][0][i]) for i in range(K)] for j in range(len(state))]
     ms = max_over_ranks(ms, dist, dev)
     status = sum(csrk.device_status(s["h"]) for s in state)
     if status:
@@ -299,6 +303,7 @@ def run_ours(args, world, rank, local):
                                  "kernel_gflops": round(2.0 * inf["nnz"] / (km * 1e-3) / 1e9, 1),
                                  "kernel_gbs": round(b / (km * 1e-3) / 1e9, 1),
                                  "kernel_frac_of_peak": round(b / (km * 1e-3) / 1e9 / peak, 3),
+                                 "permute_us": round(statistics.mean(perm_ms[j]) * 1e3, 2),
                                  "sr": inf["sr"], "ssr": inf["ssr"], "config": s["cfg"],
                                  "setup_s": round(s["tune_s"], 2)}
 
@@ -392,7 +397,7 @@ def run_ours(args, world, rank, local):
             "e2e": e2e,
             "cg": cg,
             "batch": batch,
-            "gpu_launches": K * 3 * len(state),
+            "gpu_launches": K * 2 * len(state),   # per matrix: permute x, CSR-3 kernel (+ fused unpermute)
             "clocks": clocks,
             "cpu_baseline": cpu,
             "wall_s_timed": round(wall, 3),

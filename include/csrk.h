@@ -71,6 +71,9 @@ typedef enum {
 #define CSRK_HOST_VECTORS 8u  /* x and y are HOST pointers: the call copies x in and y out
                                  through its own device scratch and returns after the
                                  copy of y has completed (synchronous) */
+#define CSRK_X_PERMUTED  16u  /* SpMV only: x is already in the reordered numbering (e.g.
+                                 from csrk_permute), y is in the input numbering; the kernel
+                                 writes row r's result to y[perm[r]] directly */
 
 /* Reordering methods for csrk_reorder. */
 #define CSRK_REORDER_NONE 0   /* keep the input numbering (perm = identity) */
@@ -131,8 +134,9 @@ int csrk_set_pointers(csrk_handle h, int32_t nsr, const int32_t* sr_ptr, int32_t
  *   flags   CSRK_VEC_PERMUTED | CSRK_ACC_F32 | CSRK_X_F32 | CSRK_HOST_VECTORS
  *   stream  cudaStream_t (NULL = default stream)
  * FP64 values with CSRK_X_F32 are CSRK_ERR_UNSUPPORTED.  Without CSRK_VEC_PERMUTED the
- * call permutes x into library scratch, runs the CSR-k kernel there and scatters the
- * result back (y[perm[i]] = result[i]).  Errors: CSRK_ERR_STATE before the pointers
+ * call permutes x into library scratch (x_p[i] = x[perm[i]]) and runs the CSR-k kernel,
+ * which stores each row's result straight to its place in the input numbering,
+ * y[perm[i]] (and reads y there when beta != 0).  Errors: CSRK_ERR_STATE before the pointers
  * exist, CSRK_ERR_ARG, CSRK_ERR_ALLOC, CSRK_ERR_CUDA. */
 int csrk_spmv(csrk_handle h, double alpha, const void* x, double beta, void* y,
               unsigned flags, void* stream);
@@ -270,7 +274,13 @@ int csrk_model_sizes(double rdensity, int arch, int32_t* ssrs, int32_t* srs);
 
 /* csrk_tuned_config: the launch configuration the handle will use (any pointer may be
  * NULL):
- *   kernel   0 = TMA-staged super-super-row kernel, 1 = direct-load kernel
+ *   kernel   0 = TMA-staged super-super-row kernel, 1 = direct-load kernel, 2 / 3 = the
+ *            same for FP64 handles with the values stored as (hi, lo) FP32 pairs and the
+ *            row sums kept as FP32 pairs: FP64 accuracy (per entry within ~7e-13 of
+ *            sum |a_ij x_j| for rows up to 48 entries) on the FP32 pipes, which on GB300
+ *            run 58x the FP64 FMA rate.  Available when every value is 0 or has magnitude
+ *            in [2^-39, 2^60] and no row exceeds 48 entries; x entries outside that range
+ *            are multiplied in FP64 individually.  SpMV only (SpMM uses 0 / 1)
  *   lanes    lanes cooperating on one row (SpMV): 1, 2, 4, 8 or 32
  *   unroll   x gathers a lane issues before consuming them; compiled (lanes, unroll)
  *            pairs: (1,4) (1,8) (1,16) (1,32) (2,8) (2,16) (4,8) (8,8) (32,4)

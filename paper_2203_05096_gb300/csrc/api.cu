@@ -64,7 +64,7 @@ void free_device(csrk_matrix* h) {
         cudaFree(v);
         v = nullptr;
     }
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < 6; ++i) {
         cudaFree(h->d_scratch[i]);
         h->d_scratch[i] = nullptr;
         h->scratch_bytes[i] = 0;
@@ -133,6 +133,11 @@ int ensure_vals(csrk_matrix* h, int vt) {
     const CsrHost& m = h->m;
     const size_t nnz = m.vals.size();
     if (vt == VAL_F64) return upload_padded(reinterpret_cast<double**>(&h->d_vals[vt]), m.vals.data(), nnz, 8, "vals");
+    if (vt == VAL_DS) {
+        std::vector<float> tmp(2 * nnz);
+        h->pairs_ok = split_pairs(m.vals.data(), tmp.data(), (int64_t)nnz) ? 1 : 0;
+        return upload_padded(reinterpret_cast<uint64_t**>(&h->d_vals[vt]), tmp.data(), nnz, 8, "vals pairs");
+    }
     if (vt == VAL_F32) {
         std::vector<float> tmp(nnz);
         narrow_f32(m.vals.data(), tmp.data(), (int64_t)nnz);
@@ -192,6 +197,17 @@ KernelConfig default_config(const csrk_matrix* h) {
     return c;
 }
 
+// The FP32-pair FP64 path needs FP64 storage, every value in [2^-39, 2^60] (or 0) and rows
+// of at most 48 entries (its error bound grows with the row length).
+bool pairs_available(csrk_matrix* h) {
+    if (h->dtype != CSRK_F64 || h->stats.max_row_len > 48) return false;
+    if (h->pairs_ok < 0) {
+        std::vector<float> tmp(2 * h->m.vals.size());
+        h->pairs_ok = split_pairs(h->m.vals.data(), tmp.data(), (int64_t)h->m.vals.size()) ? 1 : 0;
+    }
+    return h->pairs_ok == 1;
+}
+
 int smem_budget(const csrk_matrix* h, int ctas) {
     int per_cta = h->smem_per_sm / std::max(1, ctas) - 1024;
     return std::min(per_cta, h->smem_optin);
@@ -226,6 +242,7 @@ bool csrk::plan_stages(const TileStats& st, int val_bytes, int max_smem, int wan
 
 int csrk::launch_csr3(const LaunchArgs& a, const KernelConfig& cfg, const StagePlan& plan,
                       void* stream) {
+    if (cfg.kernel >= 2) return launch_csr3_ds(a, cfg, plan, stream);
     switch (a.val_type) {
         case VAL_F64: return launch_csr3_f64(a, cfg, plan, stream);
         case VAL_F32: return launch_csr3_f32(a, cfg, plan, stream);
@@ -242,15 +259,22 @@ int resolve_config(csrk_matrix* h, int vt, KernelConfig& cfg, StagePlan& plan) {
     // (the inner SpMV of a mixed-precision solve) start from the default shape
     cfg = (h->cfg_set && vt == (int)h->dtype) ? h->cfg : default_config(h);
     plan = StagePlan{};
+    if (cfg.kernel >= 2 && (vt != VAL_F64 || !pairs_available(h))) {
+        if (h->kernel_forced && vt == (int)h->dtype)
+            return fail(CSRK_ERR_UNSUPPORTED, "the FP32-pair FP64 path needs FP64 values in [2^-39, 2^60] "
+                                              "and rows of at most 48 entries");
+        cfg.kernel -= 2;
+    }
+    if (cfg.kernel >= 2 && cfg.unroll != 4 && cfg.unroll != 8 && cfg.unroll != 16) cfg.unroll = 8;
     if (cfg.ctas == 0)
-        cfg.ctas = (cfg.kernel == 0 &&
+        cfg.ctas = ((cfg.kernel == 0 || cfg.kernel == 2) &&
                     plan_stages(h->stats, (int)val_size(vt), smem_budget(h, 2), cfg.stages, plan)) ? 2 : 1;
-    if (cfg.kernel == 0) {
+    if (cfg.kernel == 0 || cfg.kernel == 2) {
         if (!plan_stages(h->stats, (int)val_size(vt), smem_budget(h, cfg.ctas), cfg.stages, plan)) {
             if (h->kernel_forced && vt == (int)h->dtype)
                 return fail(CSRK_ERR_UNSUPPORTED, "super-super-rows too large for two shared-memory stages; "
                                                   "choose smaller sizes or the direct kernel");
-            cfg.kernel = 1;   // the SSRs do not fit: fall back to direct loads
+            cfg.kernel += 1;   // the SSRs do not fit: fall back to direct loads
         }
     }
     return CSRK_OK;
@@ -280,8 +304,19 @@ int compute(csrk_matrix* h, int32_t k, bool spmm, double alpha, const void* X, i
 
     const size_t esz = x_f32 ? 4 : 8;
     const bool host_vec = flags & CSRK_HOST_VECTORS;
+    const bool x_only = (flags & CSRK_X_PERMUTED) && !(flags & CSRK_VEC_PERMUTED) && !h->perm.empty();
+    if (x_only && spmm) return fail(CSRK_ERR_UNSUPPORTED, "CSRK_X_PERMUTED is for csrk_spmv");
     const bool permuted = (flags & CSRK_VEC_PERMUTED) || h->perm.empty();
     cudaStream_t s = (cudaStream_t)stream;
+    KernelConfig cfg;
+    StagePlan plan;
+    if ((rc = resolve_config(h, vt, cfg, plan))) return rc;
+    if (spmm && cfg.kernel >= 2) cfg.kernel -= 2;   // the pair path is SpMV only
+    if (cfg.kernel >= 2) {
+        if ((rc = ensure_vals(h, VAL_DS)) || (rc = ensure_scratch(h, 4, (size_t)n * 8)) ||
+            (rc = ensure_scratch(h, 5, 16)))
+            return rc;
+    }
     const void* xin = X;
     void* yout = Y;
     int64_t ldxin = ldx, ldyout = ldy;
@@ -298,30 +333,46 @@ int compute(csrk_matrix* h, int32_t k, bool spmm, double alpha, const void* X, i
     const void* xk = xin;
     void* yk = yout;
     int64_t ldxk = ldxin, ldyk = ldyout;
-    if (!permuted) {
+    // SpMV in the input numbering stores row r's result straight to y[perm[r]] (the kernel
+    // reads y there too when beta != 0): no permuted copy of y, no separate unpermute
+    const bool fuse_y = !permuted && !spmm;
+    if (!permuted && !x_only) {
         const size_t b = (size_t)n * k * esz;
         if ((rc = ensure_scratch(h, 0, b))) return rc;
-        if ((rc = ensure_scratch(h, 1, b))) return rc;
-        int e = launch_gather_rows(xin, ldxin, h->d_scratch[0], k, h->d_perm, n, k, (int)esz, s);
-        if (e) return cuda_fail((cudaError_t)e, "permute x");
-        if (beta != 0.0) {
-            e = launch_gather_rows(yout, ldyout, h->d_scratch[1], k, h->d_perm, n, k, (int)esz, s);
+        if (!fuse_y && (rc = ensure_scratch(h, 1, b))) return rc;
+        if (cfg.kernel < 2) {
+            int e = launch_gather_rows(xin, ldxin, h->d_scratch[0], k, h->d_perm, n, k, (int)esz, s);
+            if (e) return cuda_fail((cudaError_t)e, "permute x");
+        }
+        if (beta != 0.0 && !fuse_y) {
+            int e = launch_gather_rows(yout, ldyout, h->d_scratch[1], k, h->d_perm, n, k, (int)esz, s);
             if (e) return cuda_fail((cudaError_t)e, "permute y");
         }
         xk = h->d_scratch[0];
-        yk = h->d_scratch[1];
-        ldxk = ldyk = k;
+        ldxk = k;
+        if (!fuse_y) {
+            yk = h->d_scratch[1];
+            ldyk = k;
+        }
     }
-    KernelConfig cfg;
-    StagePlan plan;
-    if ((rc = resolve_config(h, vt, cfg, plan))) return rc;
+    const void* xkern = xk;
+    if (cfg.kernel >= 2) {   // permute (when needed) and split x in one pass
+        const bool gather = !permuted && !x_only;
+        int e = launch_split_pairs(static_cast<const double*>(xin), gather ? h->d_perm : nullptr, n,
+                                   gather ? static_cast<double*>(h->d_scratch[0]) : nullptr,
+                                   h->d_scratch[4], static_cast<int32_t*>(h->d_scratch[5]), s);
+        if (e) return cuda_fail((cudaError_t)e, "split x");
+        xkern = h->d_scratch[4];
+    }
     LaunchArgs a{};
     a.desc = h->d_desc;
     a.sr_ptr = h->d_sr_ptr;
     a.rowptr = h->d_rowptr;
     a.colidx = h->d_colidx;
-    a.vals = h->d_vals[vt];
-    a.x = xk;
+    a.vals = h->d_vals[cfg.kernel >= 2 ? (int)VAL_DS : vt];
+    a.x = xkern;
+    a.x64 = static_cast<const double*>(xk);
+    a.xflag = static_cast<const int32_t*>(h->d_scratch[5]);
     a.y = yk;
     a.ldx = ldxk;
     a.ldy = ldyk;
@@ -330,6 +381,7 @@ int compute(csrk_matrix* h, int32_t k, bool spmm, double alpha, const void* X, i
     a.alpha = alpha;
     a.beta = beta;
     a.skip = nullptr;
+    a.yperm = fuse_y ? h->d_perm : nullptr;
     a.status = h->d_status;
     a.stats = h->stats;
     a.val_type = vt;
@@ -341,7 +393,7 @@ int compute(csrk_matrix* h, int32_t k, bool spmm, double alpha, const void* X, i
     int e = launch_csr3(a, cfg, plan, s);
     if (e == -1) return fail(CSRK_ERR_UNSUPPORTED, "kernel variant not compiled for this configuration");
     if (e) return cuda_fail((cudaError_t)e, "CSR-3 kernel launch");
-    if (!permuted) {
+    if (!permuted && !fuse_y) {
         e = launch_scatter_rows(h->d_scratch[1], k, yout, ldyout, h->d_perm, n, k, (int)esz, s);
         if (e) return cuda_fail((cudaError_t)e, "unpermute y");
     }
@@ -359,13 +411,25 @@ int launch_spmv_dev(csrk_matrix* h, int vt, const void* x, void* y, double alpha
     StagePlan plan;
     int rc;
     if ((rc = resolve_config(h, vt, cfg, plan))) return rc;
+    const void* xkern = x;
+    if (cfg.kernel >= 2) {
+        if ((rc = ensure_vals(h, VAL_DS)) || (rc = ensure_scratch(h, 4, (size_t)h->m.n * 8)) ||
+            (rc = ensure_scratch(h, 5, 16)))
+            return rc;
+        const int e = launch_split_pairs(static_cast<const double*>(x), nullptr, h->m.n, nullptr,
+                                         h->d_scratch[4], static_cast<int32_t*>(h->d_scratch[5]), s);
+        if (e) return cuda_fail((cudaError_t)e, "split x");
+        xkern = h->d_scratch[4];
+    }
     LaunchArgs a{};
     a.desc = h->d_desc;
     a.sr_ptr = h->d_sr_ptr;
     a.rowptr = h->d_rowptr;
     a.colidx = h->d_colidx;
-    a.vals = h->d_vals[vt];
-    a.x = x;
+    a.vals = h->d_vals[cfg.kernel >= 2 ? (int)VAL_DS : vt];
+    a.x = xkern;
+    a.x64 = static_cast<const double*>(x);
+    a.xflag = static_cast<const int32_t*>(h->d_scratch[5]);
     a.y = y;
     a.ldx = a.ldy = 1;
     a.k = 1;
@@ -535,13 +599,15 @@ int autotune(csrk_matrix* h) {
     if (rdens <= 32) pairs = {{1, 4}, {1, 8}, {1, 16}, {2, 8}};
     else if (rdens <= 64) pairs = {{2, 8}, {2, 16}, {4, 8}};
     else pairs = {{4, 8}, {8, 8}, {32, 4}};
+    const bool with_pairs = pairs_available(h);
     for (size_t b = 0; b < std::min<size_t>(3, phase1.size()) && rc == CSRK_OK; ++b) {
         if ((rc = set_fixed(h, phase1[b].sr, phase1[b].ssr)) || (rc = ensure_struct(h))) break;
         for (auto& pr : pairs)
             for (int warps : {8, 16})
-                for (int kernel : {0, 1})
+                for (int kernel : {0, 1, 2, 3})
                     for (int ctas : {1, 2}) {
-                        if (kernel == 1 && ctas == 2) continue;
+                        if ((kernel == 1 || kernel == 3) && ctas == 2) continue;
+                        if (kernel >= 2 && (!with_pairs || pr.first != 1 || pr.second > 16)) continue;
                         KernelConfig c;
                         c.kernel = kernel;
                         c.lanes = pr.first;
@@ -551,7 +617,7 @@ int autotune(csrk_matrix* h) {
                         c.stages = 0;
                         h->cfg = c;
                         h->cfg_set = true;
-                        h->kernel_forced = (kernel == 0);
+                        h->kernel_forced = (kernel != 1);
                         const float us = time_launches(h, s, e0, e1, reps);
                         if (us < best.us) {
                             best.sr = phase1[b].sr;
@@ -835,9 +901,9 @@ int csrk_set_config(csrk_handle h, int32_t kernel, int32_t lanes, int32_t unroll
     if (!h) return fail(CSRK_ERR_ARG, "handle is NULL");
     KernelConfig c = h->cfg_set ? h->cfg : default_config(h);
     if (kernel >= 0) {
-        if (kernel > 1) return fail(CSRK_ERR_ARG, "kernel must be 0 or 1");
+        if (kernel > 3) return fail(CSRK_ERR_ARG, "kernel must be 0, 1, 2 or 3");
         c.kernel = kernel;
-        h->kernel_forced = (kernel == 0);
+        h->kernel_forced = (kernel != 1);
     }
     if (lanes >= 0) {
         if (lanes != 1 && lanes != 2 && lanes != 4 && lanes != 8 && lanes != 32)
@@ -846,6 +912,8 @@ int csrk_set_config(csrk_handle h, int32_t kernel, int32_t lanes, int32_t unroll
         if (unroll < 0) c.unroll = default_unroll(lanes, h->have_ptrs ? h->stats.max_row_len : 32);
     }
     if (unroll >= 0) c.unroll = unroll;
+    if (c.kernel >= 2 && (c.lanes != 1 || (c.unroll != 4 && c.unroll != 8 && c.unroll != 16)))
+        return fail(CSRK_ERR_ARG, "kernels 2 and 3 take lanes 1 and unroll 4, 8 or 16");
     if (!pair_compiled(c.lanes, c.unroll))
         return fail(CSRK_ERR_ARG, "unsupported (lanes, unroll) pair; compiled: (1,4) (1,8) (1,16) "
                                   "(1,32) (2,8) (2,16) (4,8) (8,8) (32,4)");

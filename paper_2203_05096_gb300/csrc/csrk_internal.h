@@ -54,14 +54,19 @@ void build_descs(const CsrHost& b, const std::vector<int32_t>& sr_ptr,
                  TileStats& st);
 void narrow_f32(const double* in, float* out, int64_t n);
 void narrow_bf16(const double* in, uint16_t* out, int64_t n);
+// (hi, lo) FP32 pairs of FP64 values; returns true when every value is 0 or has magnitude
+// in [2^-39, 2^60] (the range in which the pair arithmetic keeps FP64 accuracy).
+bool split_pairs(const double* in, float* out, int64_t n);
 uint16_t f64_to_bf16(double d);
 void parallel_for(int64_t n, int64_t grain, void (*fn)(int64_t, int64_t, void*), void* ctx);
 
 // ------------------------------------------------------------------ launches
-enum ValType { VAL_F64 = 0, VAL_F32 = 1, VAL_BF16 = 2 };
+// VAL_DS: FP64 values stored as (hi, lo) FP32 pairs for the FP32-pipe FP64 path.
+enum ValType { VAL_F64 = 0, VAL_F32 = 1, VAL_BF16 = 2, VAL_DS = 3 };
 
 struct KernelConfig {
-    int kernel = 0;    // 0 TMA-staged, 1 direct loads
+    int kernel = 0;    // 0 TMA-staged, 1 direct loads; 2 / 3 the same with FP64 values as
+                       // FP32 pairs and FP32-pipe arithmetic (FP64 handles only)
     int lanes = 1;     // lanes per row (SpMV)
     int unroll = 8;    // x gathers issued per lane before the FMAs consume them
     int warps = 8;     // consumer warps per CTA
@@ -83,6 +88,9 @@ struct LaunchArgs {
     int32_t nssr;
     double alpha, beta;
     const int32_t* skip;  // optional device flag: non-zero makes the launch a no-op
+    const double* x64;    // pair kernels: the FP64 x (x then holds the FP32-pair split)
+    const int32_t* yperm; // SpMV: row r's result goes to y[yperm[r]] (fused unpermute)
+    const int32_t* xflag; // pair kernels: split found an out-of-range element
     int32_t* status;
     TileStats stats;
     int val_type;       // ValType
@@ -108,6 +116,7 @@ int launch_csr3(const LaunchArgs& a, const KernelConfig& cfg, const StagePlan& p
 int launch_csr3_f64(const LaunchArgs& a, const KernelConfig& cfg, const StagePlan& plan, void* stream);
 int launch_csr3_f32(const LaunchArgs& a, const KernelConfig& cfg, const StagePlan& plan, void* stream);
 int launch_csr3_bf16(const LaunchArgs& a, const KernelConfig& cfg, const StagePlan& plan, void* stream);
+int launch_csr3_ds(const LaunchArgs& a, const KernelConfig& cfg, const StagePlan& plan, void* stream);
 
 // api.cu: message returned by csrk_last_error() for the calling thread.
 void set_last_error(const std::string& msg);
@@ -115,6 +124,11 @@ void set_last_error(const std::string& msg);
 // vec_kernels.cu
 int launch_gather_rows(const void* in, int64_t ldi, void* out, int64_t ldo, const int32_t* perm,
                        int32_t n, int32_t k, int elem_bytes, void* stream);
+// Split FP64 x (gathered through perm when given) into FP32 pairs for the pair kernels;
+// also writes the gathered FP64 values to x64 when non-NULL; *flag = 1 when any element is
+// outside the pair range (the flag is cleared first, on the same stream).
+int launch_split_pairs(const double* in, const int32_t* perm, int32_t n, double* x64, void* pairs,
+                       int32_t* flag, void* stream);
 int launch_bounded_wait_probe(unsigned long long timeout_ns, int32_t* status, void* stream);
 int launch_scatter_rows(const void* in, int64_t ldi, void* out, int64_t ldo, const int32_t* perm,
                         int32_t n, int32_t k, int elem_bytes, void* stream);

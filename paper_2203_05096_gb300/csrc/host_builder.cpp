@@ -3,6 +3,7 @@
 // FP32 / BF16 narrowing.  Everything here is integer or bit-exact work: the same inputs
 // give the same arrays on every host.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <numeric>
 #include <thread>
@@ -382,6 +383,19 @@ uint16_t f64_to_bf16(double d) {
     // subnormal target: keep counts quanta of 2^-133; keep == 0x80 is the smallest normal,
     // whose encoding (exponent field 1, fraction 0) is the same bit pattern.
     return (uint16_t)(sign | (uint16_t)keep);
+}
+
+bool split_pairs(const double* in, float* out, int64_t n) {
+    bool ok = true;
+    for (int64_t i = 0; i < n; ++i) {
+        const double a = in[i];
+        const float h = (float)a;
+        out[2 * i] = h;
+        out[2 * i + 1] = (float)(a - (double)h);   // a - h is exact in FP64
+        const double m = std::fabs(a);
+        if (a != 0.0 && !(m >= 0x1p-39 && m <= 0x1p60)) ok = false;
+    }
+    return ok;
 }
 
 void narrow_bf16(const double* in, uint16_t* out, int64_t n) {

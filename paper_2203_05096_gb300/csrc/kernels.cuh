@@ -149,6 +149,59 @@ template <> struct Acc<float> {
     }
 };
 
+// ------------------------------------------------------------------ FP64 on FP32 pipes
+// A stored FP64 value a as an (hi, lo) pair of FP32 values with hi = RN(a) and
+// lo = RN(a - hi): 48 significant bits, |a - hi - lo| <= 2^-48 |a|.  Built on the host.
+struct ds_t { float hi, lo; };
+template <> struct Val<ds_t> { static constexpr int bytes = 8; };
+
+// The FP64 value of a stored pair (exact: the two halves do not overlap).
+__device__ __forceinline__ double ds_value(const ds_t a) { return x_f64(a.hi) + x_f64(a.lo); }
+
+// An FP64 x value as an (hi, lo) FP32 pair: hi its top 24 significant bits, lo the next
+// 24 (rounded), |x - hi - lo| <= 2^-48 |x|.  Built once per SpMV by split_pairs_kernel,
+// which also flags any x outside [2^-39, 2^60] (non-zero) or non-finite.
+struct xpair { float hi, lo; };
+
+// Split one FP64 value with integer instructions.  Returns false when x is outside the
+// pair range (x = 0 splits to (0, 0) and is in range).
+__device__ __forceinline__ bool split_x(double x, xpair& out) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    const uint32_t hi = (uint32_t)(u >> 32), lo = (uint32_t)u;
+    const uint32_t e = (hi >> 20) & 0x7FFu;
+    if (e - 984u <= 99u) {   // biased exponent 984..1083: 2^-39 <= |x| < 2^61
+        const uint32_t sgn = hi & 0x80000000u;
+        out.hi = __uint_as_float(sgn | ((e - 896u) << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29));
+        // the remaining 29 bits, exactly as an integer-valued float via the 2^23 trick on
+        // their top 23 bits, then scaled by a power of two
+        const float m = __fsub_rn(__uint_as_float(0x4B000000u | ((lo >> 6) & 0x7FFFFFu)), 8388608.0f);
+        out.lo = __fmul_rn(m, __uint_as_float(sgn | ((e - 942u) << 23)));
+        return true;
+    }
+    out.hi = 0.f;
+    out.lo = 0.f;
+    return ((hi & 0x7FFFFFFFu) | lo) == 0;
+}
+
+// s += a * x for one nonzero with the row sum held as an unevaluated pair (sh + sl) of FP32
+// values: a*x = p + ep + (a.hi*x.lo + a.lo*x.hi) up to 2^-45 |a x| (p = RN(a.hi*x.hi), ep its
+// exact error by FMA, a.lo*x.lo dropped); p enters by TwoSum, the small terms go to sl, and
+// (sh, sl) is renormalised by Fast2Sum so |sl| <= ulp(sh) / 2.  Over a row of m <= 48
+// entries the error stays below 1e-12 of sum |a x|.  Explicit round-to-nearest intrinsics
+// keep the compiler from contracting or reassociating the error-free transforms.
+__device__ __forceinline__ void ds_accum(const ds_t a, const xpair x, float& sh, float& sl) {
+    const float p = __fmul_rn(a.hi, x.hi);
+    const float ep = __fmaf_rn(a.hi, x.hi, -p);
+    const float t = __fmaf_rn(a.hi, x.lo, __fmaf_rn(a.lo, x.hi, ep));
+    const float s = __fadd_rn(sh, p);
+    const float bp = __fsub_rn(s, sh);
+    const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, bp)), __fsub_rn(p, bp));
+    const float l = __fadd_rn(sl, __fadd_rn(err, t));
+    const float s2 = __fadd_rn(s, l);
+    sl = __fsub_rn(l, __fsub_rn(s2, s));
+    sh = s2;
+}
+
 template <typename T>
 __device__ __forceinline__ T ldg_x(const T* p) { return __ldg(p); }
 
@@ -188,7 +241,8 @@ __device__ __forceinline__ void spmv_rows(int rb, int re, const int32_t* __restr
                                           const int32_t* __restrict__ col_s,
                                           const VT* __restrict__ val_s,
                                           const XT* __restrict__ x, XT* __restrict__ y,
-                                          double alpha, double beta, int epi, int lane) {
+                                          double alpha, double beta, int epi, int lane,
+                                          const int32_t* __restrict__ yperm = nullptr) {
     constexpr int RPP = 32 / LPR;   // rows per pass
     constexpr int T = U < 4 ? U : 4;
     const int sub = lane % LPR;
@@ -224,7 +278,59 @@ __device__ __forceinline__ void spmv_rows(int rb, int re, const int32_t* __restr
             for (int off = LPR / 2; off > 0; off >>= 1)
                 acc += __shfl_xor_sync(0xffffffffu, acc, off);
         }
-        if (r < re && sub == 0) store_y<XT, AT>(y, r, acc, alpha, beta, epi);
+        if (r < re && sub == 0) store_y<XT, AT>(y, yperm ? __ldg(&yperm[r]) : r, acc, alpha, beta, epi);
+    }
+}
+
+// spmv_rows for FP64 values stored as (hi, lo) FP32 pairs: one row per lane.  Fast path
+// (x2 = x split into pairs, every element in range): the row sum in FP32 pairs (ds_accum),
+// chunks of U pair gathers issued before their accumulations.  When the split pass flagged
+// an element (`slow`), the launch multiplies in FP64 from the pairs' exact FP64 values and
+// the FP64 x instead.
+template <int U>
+__device__ __forceinline__ void spmv_rows_ds(int rb, int re, const int32_t* __restrict__ rp,
+                                             const int32_t* __restrict__ col_s,
+                                             const ds_t* __restrict__ val_s,
+                                             const xpair* __restrict__ x2,
+                                             const double* __restrict__ x64, bool slow,
+                                             double* __restrict__ y, double alpha, double beta,
+                                             int epi, int lane, const int32_t* __restrict__ yperm) {
+    for (int base = rb; base < re; base += 32) {
+        const int r = base + lane;
+        if (r >= re) continue;
+        const int pe = rp[r + 1];
+        int c = rp[r];
+        double acc;
+        if (!slow) {
+            float sh = 0.f, sl = 0.f;
+            for (; c + U <= pe; c += U) {
+                xpair xv[U];
+#pragma unroll
+                for (int t = 0; t < U; ++t) {
+                    const float2 v = __ldg(reinterpret_cast<const float2*>(x2) + col_s[c + t]);
+                    xv[t] = xpair{v.x, v.y};
+                }
+#pragma unroll
+                for (int t = 0; t < U; ++t) ds_accum(val_s[c + t], xv[t], sh, sl);
+            }
+            for (; c < pe; c += 4) {
+                xpair xv[4];
+#pragma unroll
+                for (int t = 0; t < 4; ++t)
+                    if (c + t < pe) {
+                        const float2 v = __ldg(reinterpret_cast<const float2*>(x2) + col_s[c + t]);
+                        xv[t] = xpair{v.x, v.y};
+                    }
+#pragma unroll
+                for (int t = 0; t < 4; ++t)
+                    if (c + t < pe) ds_accum(val_s[c + t], xv[t], sh, sl);
+            }
+            acc = x_f64(sh) + x_f64(sl);
+        } else {
+            acc = 0.0;
+            for (; c < pe; ++c) acc = fma(ds_value(val_s[c]), __ldg(&x64[col_s[c]]), acc);
+        }
+        store_y<double, double>(y, yperm ? __ldg(&yperm[r]) : r, acc, alpha, beta, epi);
     }
 }
 
@@ -308,6 +414,9 @@ struct TmaParams {
     double alpha, beta;
     int32_t epi;   // EPI_SCALE | EPI_ACCUM
     const int32_t* skip;   // optional: non-zero on the device means "do nothing"
+    const double* x64;     // MODE 2: FP64 x (P.x then holds its FP32-pair split)
+    const int32_t* yperm;  // SpMV: when set, row r's result goes to y[yperm[r]] (fused unpermute)
+    const int32_t* xflag;  // MODE 2: non-zero when the split found an out-of-range element
     int32_t* status;
     uint32_t off_srp, off_rp, off_col, off_val, stage_bytes, header_bytes;
     int32_t stages;
@@ -324,7 +433,8 @@ __device__ __forceinline__ void slice16(int64_t first, int64_t last_excl, int64_
 }
 
 // MODE 0: SpMV with LPR lanes per row and gather chunks of U.  MODE 1: SpMM with G = LPR
-// lanes per row and U columns per lane.
+// lanes per row and U columns per lane.  MODE 2: SpMV with FP64 values as FP32 pairs
+// (VT = ds_t, one row per lane, FP64 accuracy on the FP32 pipes).
 // At most 60 registers per thread, so two blocks of 16 consumer warps + 1 producer warp
 // fit on one SM (65,536 registers).
 template <typename VT, typename XT, typename AT, int LPR, int MODE, int U>
@@ -383,6 +493,8 @@ __global__ void __launch_bounds__(544, 2) csr3_tma_kernel(const TmaParams P) {
 
     // ---------------- consumers
     const XT* __restrict__ x = static_cast<const XT*>(P.x);
+    const bool slow = MODE == 2 && P.xflag && *P.xflag;
+    (void)slow;
     XT* __restrict__ y = static_cast<XT*>(P.y);
     int i = 0;
     int sr_seq = 0;   // index of the next super-row in this block's stream
@@ -407,9 +519,12 @@ __global__ void __launch_bounds__(544, 2) csr3_tma_kernel(const TmaParams P) {
         for (int j = first; j < nsr; j += W) {
             const int sr = d.s0 + j;
             const int rb = srp[sr], re = srp[sr + 1];
-            if constexpr (MODE == 0)
+            if constexpr (MODE == 2)
+                spmv_rows_ds<U>(rb, re, rp, col, val, reinterpret_cast<const xpair*>(P.x), P.x64,
+                                slow, y, P.alpha, P.beta, P.epi, lane, P.yperm);
+            else if constexpr (MODE == 0)
                 spmv_rows<VT, XT, AT, LPR, U>(rb, re, rp, col, val, x, y, P.alpha, P.beta, P.epi,
-                                              lane);
+                                              lane, P.yperm);
             else
                 spmm_rows<VT, XT, AT, LPR, U>(rb, re, rp, col, val, x, P.ldx, y, P.ldy, P.k,
                                                P.alpha, P.beta, P.epi, lane);
@@ -430,15 +545,20 @@ __global__ void __launch_bounds__(512, 1) csr3_direct_kernel(const TmaParams P) 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int W = blockDim.x >> 5;
     const XT* __restrict__ x = static_cast<const XT*>(P.x);
+    const bool slow = MODE == 2 && P.xflag && *P.xflag;
+    (void)slow;
     XT* __restrict__ y = static_cast<XT*>(P.y);
     const VT* __restrict__ vals = static_cast<const VT*>(P.vals);
     for (int t = blockIdx.x; t < P.nssr; t += gridDim.x) {
         const SsrDesc d = P.desc[t];
         for (int sr = d.s0 + warp; sr < d.s1; sr += W) {
             const int rb = __ldg(&P.sr_ptr[sr]), re = __ldg(&P.sr_ptr[sr + 1]);
-            if constexpr (MODE == 0)
+            if constexpr (MODE == 2)
+                spmv_rows_ds<U>(rb, re, P.rowptr, P.colidx, vals, reinterpret_cast<const xpair*>(P.x),
+                                P.x64, slow, y, P.alpha, P.beta, P.epi, lane, P.yperm);
+            else if constexpr (MODE == 0)
                 spmv_rows<VT, XT, AT, LPR, U>(rb, re, P.rowptr, P.colidx, vals, x, y, P.alpha,
-                                              P.beta, P.epi, lane);
+                                              P.beta, P.epi, lane, P.yperm);
             else
                 spmm_rows<VT, XT, AT, LPR, U>(rb, re, P.rowptr, P.colidx, vals, x, P.ldx, y,
                                                P.ldy, P.k, P.alpha, P.beta, P.epi, lane);

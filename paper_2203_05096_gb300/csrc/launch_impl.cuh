@@ -27,6 +27,9 @@ static int launch_one(const LaunchArgs& a, const KernelConfig& cfg, const StageP
     P.beta = a.beta;
     P.epi = (a.alpha != 1.0 ? EPI_SCALE : 0) | (a.beta != 0.0 ? EPI_ACCUM : 0);
     P.skip = a.skip;
+    P.x64 = a.x64;
+    P.yperm = a.yperm;
+    P.xflag = a.xflag;
     P.status = a.status;
     P.off_srp = plan.off_srp;
     P.off_rp = plan.off_rp;

@@ -38,14 +38,17 @@ struct csrk_matrix {
     bool dev_ptrs = false;         // sr_ptr/desc uploaded
     int32_t* d_rowptr = nullptr;
     int32_t* d_colidx = nullptr;
-    void* d_vals[3] = {nullptr, nullptr, nullptr};
+    void* d_vals[4] = {nullptr, nullptr, nullptr, nullptr};   // by ValType
+    int pairs_ok = -1;             // FP32-pair path usable (values in range); -1 unknown
     int32_t* d_sr_ptr = nullptr;
     SsrDesc* d_desc = nullptr;
     int32_t* d_perm = nullptr;
     int32_t* d_status = nullptr;
     // scratch: permuted x / y, and device copies of host vectors
-    void* d_scratch[4] = {nullptr, nullptr, nullptr, nullptr};
-    size_t scratch_bytes[4] = {0, 0, 0, 0};
+    // slots: 0 permuted x, 1 permuted y, 2/3 device copies of host x/y, 4 FP32-pair split
+    // of x for the pair kernels, 5 the split's out-of-range flag
+    void* d_scratch[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    size_t scratch_bytes[6] = {0, 0, 0, 0, 0, 0};
     // conjugate-gradient workspace (cg.cu), allocated on the first solve
     struct CgWork* cg = nullptr;
     // bumped whenever pointers or the launch shape change (invalidates captured graphs)
@@ -63,6 +66,7 @@ int ensure_struct(csrk_matrix* h);
 int ensure_vals(csrk_matrix* h, int vt);
 int ensure_scratch(csrk_matrix* h, int slot, size_t bytes);
 KernelConfig default_config(const csrk_matrix* h);
+bool pairs_available(csrk_matrix* h);
 int resolve_config(csrk_matrix* h, int vt, KernelConfig& cfg, StagePlan& plan);
 int compute(csrk_matrix* h, int32_t k, bool spmm, double alpha, const void* X, int64_t ldx,
             double beta, void* Y, int64_t ldy, unsigned flags, void* stream);

@@ -19,7 +19,7 @@ _LIB = None
 
 F64, F32, BF16 = 0, 1, 2
 DTYPES = {"f64": F64, "f32": F32, "bf16": BF16, F64: F64, F32: F32, BF16: BF16}
-VEC_PERMUTED, ACC_F32, X_F32, HOST_VECTORS = 1, 2, 4, 8
+VEC_PERMUTED, ACC_F32, X_F32, HOST_VECTORS, X_PERMUTED = 1, 2, 4, 8, 16
 REORDER = {"none": 0, "rcm": 1, 0: 0, 1: 1}
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_MATRIX", 3: "ERR_STATE", 4: "ERR_ALLOC",
           5: "ERR_CUDA", 6: "ERR_UNSUPPORTED", 7: "ERR_TIMEOUT", 8: "ERR_NOT_CONVERGED"}

@@ -260,6 +260,22 @@ def test_vec_permuted_and_permute_entry_point():
     csrk.destroy(h)
 
 
+def test_x_permuted_flag_scatters_y():
+    a = small_27pt(15)
+    x = synth.uniform_vector(a.n, 28)
+    y0 = synth.uniform_vector(a.n, 29)
+    h = make(a)
+    perm = csrk.export(h)["perm"]
+    for kernel in (0, 1):
+        csrk.set_config(h, kernel=kernel)
+        xp = torch.tensor(x[perm], device=DEV)
+        yt = torch.tensor(y0, device=DEV)
+        csrk.spmv(h, 1.25, xp, -2.0, yt, csrk.X_PERMUTED)
+        torch.cuda.synchronize()
+        assert_close(yt.cpu().numpy(), a, a.vals, x, 1.25, -2.0, y0)
+    csrk.destroy(h)
+
+
 def test_host_vectors():
     a = small_27pt(12)
     x = synth.uniform_vector(a.n, 23)
@@ -317,3 +333,54 @@ def test_autotuner_picks_a_working_config():
     assert csrk.tuned_config(h2) == cfg and csrk.info(h2)["sr"] == inf["sr"]
     csrk.destroy(h)
     csrk.destroy(h2)
+
+
+# ------------------------------------------------------------------ FP64 on FP32 pipes
+@pytest.mark.parametrize("kernel,unroll", [(2, 4), (2, 8), (2, 16), (3, 4), (3, 8)])
+def test_pair_path_fp64_bound(kernel, unroll):
+    for a in (small_27pt(14), synth.fem_like(12, 5),
+              synth.random_pattern(500, 0.03, 15, empty_rows=30)):
+        x = synth.uniform_vector(a.n, 26)
+        h = make(a, 32, 4, cfg=dict(kernel=kernel, lanes=1, unroll=unroll))
+        assert csrk.tuned_config(h)["kernel"] == kernel
+        assert_close(gpu_spmv(h, x), a, a.vals, x)
+        y0 = synth.uniform_vector(a.n, 27)
+        assert_close(gpu_spmv(h, x, -0.5, 2.0, y0), a, a.vals, x, -0.5, 2.0, y0)
+        csrk.destroy(h)
+
+
+def test_pair_path_integer_exact_and_extreme_x():
+    a = synth.random_pattern(400, 0.03, 16, integer_values=True, empty_rows=20)
+    xi = np.random.default_rng(17).integers(-1000, 1001, size=a.n).astype(np.float64)
+    h = make(a, 16, 4, cfg=dict(kernel=2, lanes=1, unroll=8))
+    assert np.array_equal(gpu_spmv(h, xi), ospmv.csr_spmv(a.n, a.rowptr, a.colidx, a.vals, xi))
+    # zeros, tiny, huge and non-finite entries go through the per-element FP64 product
+    x = synth.uniform_vector(a.n, 18)
+    x[::7] = 0.0
+    x[1::11] = 1e-300
+    x[2::13] = 3e150
+    x[3::17] = -2.0 ** -45
+    got = gpu_spmv(h, x)
+    assert_close(got, a, a.vals, x)
+    xn = x.copy()
+    xn[5] = np.inf
+    xn[9] = np.nan
+    ref = ospmv.csr_spmv(a.n, a.rowptr, a.colidx, a.vals, xn)
+    got = gpu_spmv(h, xn)
+    assert np.array_equal(np.isnan(got), np.isnan(ref))
+    fin = np.isfinite(ref)
+    assert np.array_equal(got[~fin & ~np.isnan(ref)], ref[~fin & ~np.isnan(ref)])
+    csrk.destroy(h)
+
+
+def test_pair_path_refused_for_out_of_range_values():
+    a = synth.stencil_3d(8, 8, 8, 7, "random_dd", 19)
+    a.vals[5] = 1e-30                      # below 2^-39: the pair arithmetic would lose accuracy
+    x = synth.uniform_vector(a.n, 20)
+    h = make(a, 32, 4, cfg=dict(kernel=2, lanes=1, unroll=8))
+    with pytest.raises(csrk.CsrkError) as ei:
+        gpu_spmv(h, x)
+    assert ei.value.status == "ERR_UNSUPPORTED"
+    csrk.set_config(h, kernel=0)
+    assert_close(gpu_spmv(h, x), a, a.vals, x)
+    csrk.destroy(h)
