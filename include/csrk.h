@@ -201,15 +201,23 @@ int csrk_cg(csrk_handle h, const double* b, double* x, double rtol, int32_t maxi
  *   hs     count handles, each with its pointer arrays set (sizes or explicit); any
  *          value dtype; all on the current device
  *   k      right-hand sides per matrix, 1..64
- * Tiles of about 32K nonzeros (whole super-super-rows) are queued matrix by matrix
- * (matrices by decreasing work, each matrix's tiles in row order).
+ * Each matrix is cut into items, runs of whole super-rows holding at most 24 KB of
+ * staged data (rowptr, colidx and value slices rounded out to 16 bytes; at least one
+ * super-row each; the environment variable CSRK_BATCH_ITEM_BYTES overrides the 24 KB),
+ * grouped four to a tile; tiles are queued matrix by matrix (matrices by decreasing work,
+ * each matrix's tiles in row order).  When two stages of the largest item do not fit a
+ * block's shared memory (half an SM), the batch uses a direct-load kernel over tiles of
+ * about 32K nonzeros (whole super-super-rows) instead.
  * Uploads the handles' device forms if needed.  Errors: CSRK_ERR_ARG, CSRK_ERR_STATE,
  * CSRK_ERR_ALLOC, CSRK_ERR_CUDA. */
 int csrk_batch_create(const csrk_handle* hs, int32_t count, const int32_t* k,
                       csrk_batch_handle* out);
 
 /* csrk_batch_spmm: Y_i = alpha A_i X_i + beta Y_i for every matrix of the batch in one
- * persistent launch (blocks take tiles from an atomic counter; no block waits on another).
+ * persistent launch (blocks take tiles from an atomic counter; no block waits on another;
+ * in each block a producer warp stages the tiles' items into shared memory with bulk
+ * copies while the other warps compute).  Every wait inside the kernel is bounded (2 s);
+ * one that gives up sets a bit of the batch's status word (csrk_batch_device_status).
  *   X, Y    host arrays of count DEVICE pointers (X[i], Y[i]: n_i x k_i FP64 blocks)
  *   flags   must be CSRK_VEC_PERMUTED
  * A call with the same pointers as the previous one reuses the device-side table (one
@@ -237,6 +245,16 @@ int csrk_batch_cg(csrk_batch_handle b, const double* const* B, double* const* X,
  * concatenated vector (sum of n_i k_i); any pointer may be NULL. */
 int csrk_batch_info(csrk_batch_handle b, int32_t* nmat, int32_t* nsys, int32_t* ntiles,
                     int64_t* total);
+
+/* csrk_batch_plan: the staged kernel's plan -- items (0 when the direct-load kernel is
+ * used), shared-memory stages per block (0 likewise) and bytes per stage; any pointer may
+ * be NULL. */
+int csrk_batch_plan(csrk_batch_handle b, int32_t* items, int32_t* stages, int32_t* stage_bytes);
+
+/* csrk_batch_device_status: read the batch's device status word (synchronous copy):
+ * 0 = no error; bit 0 = a bounded wait in the batched SpMM kernel gave up (the launch's
+ * results are incomplete); bit 1 = an item larger than a stage was skipped.  Sticky. */
+int csrk_batch_device_status(csrk_batch_handle b, int32_t* status);
 
 /* csrk_batch_destroy: free the batch (not its handles) after synchronising the device.
  * NULL is a no-op. */

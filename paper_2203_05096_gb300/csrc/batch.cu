@@ -1,13 +1,18 @@
 // Batched work over many CSR-k matrices of uneven size.
 //
 // csrk_batch_spmm: Y_i = alpha A_i X_i + beta Y_i for every matrix i of a batch in ONE
-// persistent launch.  The work list holds tiles (matrix, range of super-super-rows),
-// matrices by decreasing work and each matrix's tiles in row order (neighbouring blocks
-// share the matrix's x window in L2); each thread block takes the next tile with an atomic counter
-// (no block ever waits for another) and runs the tile's super-rows on its warps, with the
-// row mapping of the matrix's right-hand-side count (one row per lane for k = 1, k lanes
-// per row otherwise).  The last block to finish resets the counter, so the launch can be
-// replayed from a CUDA graph.
+// persistent launch.  The batch cuts each matrix into items -- runs of whole super-rows
+// of at most 24 KB of matrix data, the batch's own super-super-rows sized to a shared-memory
+// stage -- and queues tiles of a few items matrix by matrix (matrices by decreasing work,
+// each matrix's items in row order, so the blocks running at any moment share one x
+// window in L2).  In each block a producer warp takes the next tile from an atomic
+// counter and streams its items' rowptr / colidx / value slices into a ring of shared
+// memory stages with bulk copies (cp.async.bulk, mbarrier completion); the consumer warps
+// split every staged item into row groups of one warp pass each (32 rows for k = 1, 32/G
+// rows with G >= k lanes per row otherwise) and gather x from global memory.  No block
+// ever waits for another, and no block-wide barrier is taken after the start.  The last
+// producer to finish resets the counter, so the launch can be replayed from a CUDA graph.
+// Batches whose super-rows do not fit two stages use a direct-load kernel instead.
 //
 // csrk_batch_cg: independent conjugate-gradient solves for every (matrix, right-hand side)
 // pair, FP64 vectors and scalars, each step one batched SpMM launch plus batched vector
@@ -18,6 +23,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <new>
 #include <numeric>
 #include <vector>
@@ -113,6 +119,196 @@ __global__ void __launch_bounds__(BW * 32, 4) batch_spmm_kernel(const BatchMat* 
             atomicExch(&counters[0], 0u);
             atomicExch(&counters[1], 0u);
         }
+    }
+}
+
+// ---------------------------------------------------------------- staged SpMM kernel
+// A run of whole super-rows of one matrix, staged into shared memory as one unit.
+struct BatchItem {
+    int32_t mat, r0, r1, p0, p1, pad0, pad1, pad2;
+};
+struct ItemTile {   // items [i0, i1) of one matrix, handed out by the atomic counter
+    int32_t i0, i1;
+};
+struct StageHdr {   // written by the producer before the stage's copies, read by consumers
+    int32_t mat;     // -1: no more work; -2: item skipped (did not fit; status bit 2 set)
+    int32_t r0, r1, p0;
+    uint32_t off_col, off_val;
+    int32_t pad0, pad1;
+};
+
+constexpr int TW = 16;                  // consumer warps per block (+1 producer warp)
+constexpr int MAX_STAGES = 16;
+constexpr int HDR_BYTES = MAX_STAGES * (2 * 8 + (int)sizeof(StageHdr));   // 768
+constexpr int64_t ITEM_BYTES_DEFAULT = 24576;
+constexpr size_t ITEMS_PER_TILE = 4;
+
+// Element slice [first, last) rounded out to 16-byte boundaries, element size esz.
+__host__ __device__ inline void slice16_rt(int64_t first, int64_t last, int esz, int64_t& a0, uint32_t& bytes) {
+    const int64_t per = 16 / esz;
+    a0 = first & ~(per - 1);
+    const int64_t a1 = (last + per - 1) & ~(per - 1);
+    bytes = (uint32_t)((a1 - a0) * esz);
+}
+
+__host__ __device__ inline int val_bytes_of(int vt) { return vt == csrk::VAL_F64 ? 8 : vt == csrk::VAL_F32 ? 4 : 2; }
+
+// Rows one warp pass covers for k right-hand sides (the lane mapping of sr_rows).
+__device__ __forceinline__ int rows_per_pass(int k) {
+    return k == 1 ? 32 : k == 2 ? 16 : k <= 4 ? 8 : k <= 8 ? 4 : k <= 16 ? 2 : 1;
+}
+
+// The row groups first, first + TW, ... of a staged item for one (value type, k) class.
+// rp / col / vb point into the stage; out of line like sr_rows.
+template <typename VT, int G, int CPL>
+__device__ __noinline__ void item_rows(const double* X, double* Y, int k, int r0, int r1, int p0, int first,
+                                       const int32_t* rp, const int32_t* col, const unsigned char* vb,
+                                       double alpha, double beta, int epi, int lane) {
+    using namespace csrk::dev;
+    constexpr int VPER = 16 / (int)sizeof(VT);
+    const VT* val = reinterpret_cast<const VT*>(vb) - (p0 & ~(VPER - 1));
+    constexpr int RPP = G == 1 ? 32 : 32 / G;
+    const int ng = (r1 - r0 + RPP - 1) / RPP;
+    for (int g = first; g < ng; g += TW) {
+        const int rb = r0 + g * RPP, re = min(rb + RPP, r1);
+        if constexpr (G == 1)
+            spmv_rows<VT, double, double, 1, 8>(rb, re, rp, col, val, X, Y, alpha, beta, epi, lane);
+        else
+            spmm_rows<VT, double, double, G, CPL>(rb, re, rp, col, val, X, k, Y, k, k, alpha, beta, epi, lane);
+    }
+}
+
+template <typename VT>
+__device__ __forceinline__ void item_dispatch(const BatchMat* m, int r0, int r1, int p0, int first,
+                                              const int32_t* rp, const int32_t* col, const unsigned char* vb,
+                                              double alpha, double beta, int epi, int lane) {
+    const int k = m->k;
+    const double* X = m->X;
+    double* Y = m->Y;
+    if (k == 1) item_rows<VT, 1, 1>(X, Y, k, r0, r1, p0, first, rp, col, vb, alpha, beta, epi, lane);
+    else if (k == 2) item_rows<VT, 2, 1>(X, Y, k, r0, r1, p0, first, rp, col, vb, alpha, beta, epi, lane);
+    else if (k <= 4) item_rows<VT, 4, 1>(X, Y, k, r0, r1, p0, first, rp, col, vb, alpha, beta, epi, lane);
+    else if (k <= 8) item_rows<VT, 8, 1>(X, Y, k, r0, r1, p0, first, rp, col, vb, alpha, beta, epi, lane);
+    else if (k <= 16) item_rows<VT, 16, 1>(X, Y, k, r0, r1, p0, first, rp, col, vb, alpha, beta, epi, lane);
+    else if (k <= 32) item_rows<VT, 32, 1>(X, Y, k, r0, r1, p0, first, rp, col, vb, alpha, beta, epi, lane);
+    else item_rows<VT, 32, 2>(X, Y, k, r0, r1, p0, first, rp, col, vb, alpha, beta, epi, lane);
+}
+
+// At most 60 registers per thread: two blocks of 17 warps per SM.
+__global__ void __launch_bounds__((TW + 1) * 32, 2)
+    batch_spmm_tma_kernel(const BatchMat* __restrict__ mats, const BatchItem* __restrict__ items,
+                          const ItemTile* __restrict__ tiles, int32_t ntiles, uint32_t* counters, double alpha,
+                          double beta, int epi, uint32_t stage_bytes, int32_t S, unsigned long long timeout_ns,
+                          int32_t* status) {
+    using namespace csrk::dev;
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem);
+    uint64_t* empty = full + MAX_STAGES;
+    StageHdr* hdr = reinterpret_cast<StageHdr*>(smem + 16 * MAX_STAGES);
+    unsigned char* stage0 = smem + HDR_BYTES;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], TW);
+        }
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    if (warp == TW) {
+        // ---------------- producer: one elected lane fetches tiles and issues the copies
+        if (lane == 0) {
+            const uint64_t pol = policy_evict_first();
+            int i = 0;
+            bool ok = true;
+            for (;;) {
+                const int32_t t = (int32_t)atomicAdd(&counters[0], 1u);
+                if (t >= ntiles) break;
+                const ItemTile tl = tiles[t];
+                for (int32_t q = tl.i0; q < tl.i1; ++q, ++i) {
+                    const int s = i % S;
+                    if (i >= S && !mbar_wait_bounded(&empty[s], ((i / S) - 1) & 1, timeout_ns)) {
+                        report(status, 1);
+                        ok = false;
+                        break;
+                    }
+                    const BatchItem it = items[q];
+                    const BatchMat* m = &mats[it.mat];
+                    const int esz = val_bytes_of(m->vt);
+                    int64_t o_rp, o_col, o_val;
+                    uint32_t b_rp, b_col, b_val;
+                    slice16_rt(it.r0, (int64_t)it.r1 + 1, 4, o_rp, b_rp);
+                    slice16_rt(it.p0, it.p1, 4, o_col, b_col);
+                    slice16_rt(it.p0, it.p1, esz, o_val, b_val);
+                    StageHdr h{it.mat, it.r0, it.r1, it.p0, b_rp, b_rp + b_col, 0, 0};
+                    if (b_rp + b_col + b_val > stage_bytes) {   // cannot happen for a plan built on the host
+                        report(status, 2);
+                        h.mat = -2;
+                        hdr[s] = h;
+                        mbar_arrive(&full[s]);
+                        continue;
+                    }
+                    hdr[s] = h;
+                    unsigned char* st = stage0 + (size_t)s * stage_bytes;
+                    mbar_arrive_expect_tx(&full[s], b_rp + b_col + b_val);
+                    bulk_g2s(st, m->rowptr + o_rp, b_rp, &full[s], pol);
+                    if (b_col) bulk_g2s(st + b_rp, m->colidx + o_col, b_col, &full[s], pol);
+                    if (b_val)
+                        bulk_g2s(st + b_rp + b_col, static_cast<const unsigned char*>(m->vals) + o_val * esz, b_val,
+                                 &full[s], pol);
+                }
+                if (!ok) break;
+            }
+            if (ok) {   // the end marker
+                const int s = i % S;
+                if (i >= S && !mbar_wait_bounded(&empty[s], ((i / S) - 1) & 1, timeout_ns)) {
+                    report(status, 1);
+                } else {
+                    hdr[s].mat = -1;
+                    mbar_arrive(&full[s]);
+                }
+            }
+            // the last producer out resets the tile counter for the next launch
+            __threadfence();
+            if (atomicAdd(&counters[1], 1u) == gridDim.x - 1) {
+                atomicExch(&counters[0], 0u);
+                atomicExch(&counters[1], 0u);
+            }
+        }
+        return;
+    }
+
+    // ---------------- consumers
+    int seq = 0;   // row groups of this block's stream so far, mod TW
+    for (int i = 0;; ++i) {
+        const int s = i % S;
+        if (!mbar_wait_bounded(&full[s], (i / S) & 1, timeout_ns)) {
+            report(status, 1);
+            mbar_wait_bounded(&full[s], (i / S) & 1, timeout_ns);   // let copies in flight land
+            return;
+        }
+        const StageHdr h = hdr[s];
+        if (h.mat == -1) break;
+        if (h.mat >= 0) {
+            const BatchMat* m = &mats[h.mat];
+            const unsigned char* st = stage0 + (size_t)s * stage_bytes;
+            const int32_t* rp = reinterpret_cast<const int32_t*>(st) - (h.r0 & ~3);
+            const int32_t* col = reinterpret_cast<const int32_t*>(st + h.off_col) - (h.p0 & ~3);
+            const unsigned char* vb = st + h.off_val;
+            const int rpp = rows_per_pass(m->k);
+            const int ng = (h.r1 - h.r0 + rpp - 1) / rpp;
+            const int first = (warp - seq + TW) % TW;
+            seq = (seq + ng) % TW;
+            if (first < ng) {
+                const int vt = m->vt;
+                if (vt == csrk::VAL_F64) item_dispatch<double>(m, h.r0, h.r1, h.p0, first, rp, col, vb, alpha, beta, epi, lane);
+                else if (vt == csrk::VAL_F32) item_dispatch<float>(m, h.r0, h.r1, h.p0, first, rp, col, vb, alpha, beta, epi, lane);
+                else item_dispatch<bf16_t>(m, h.r0, h.r1, h.p0, first, rp, col, vb, alpha, beta, epi, lane);
+            }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);
     }
 }
 
@@ -273,7 +469,13 @@ struct csrk_batch {
     BatchMat* d_mats_user = nullptr; // tables: user-bound vectors / internal P,Q / internal X,R
     BatchMat* d_mats_pq = nullptr;
     BatchMat* d_mats_xr = nullptr;
-    BatchTile* d_tiles = nullptr;
+    BatchTile* d_tiles = nullptr;    // direct-load kernel: tiles of whole SSRs
+    BatchItem* d_items = nullptr;    // staged kernel: items and tiles of items
+    ItemTile* d_itiles = nullptr;
+    int32_t nitems = 0, nitiles = 0;
+    uint32_t stage_bytes = 0;
+    int32_t stages = 0;              // 0: the staged kernel is not used
+    int32_t* d_status = nullptr;     // bit 0: a bounded wait gave up; bit 1: an item did not fit
     uint32_t* d_counters = nullptr;
     Chunk* d_chunks = nullptr;
     int32_t *d_sys_mat = nullptr, *d_sys_col = nullptr, *d_sys_off = nullptr;
@@ -289,6 +491,7 @@ struct csrk_batch {
     double* d_true = nullptr;
     const double** d_ptrs_in = nullptr;
     double** d_ptrs_out = nullptr;
+    unsigned long long timeout_ns = 2000000000ull;
     cudaStream_t cap = nullptr;
     cudaGraphExec_t exec = nullptr;
     int32_t exec_iters = 0;
@@ -314,7 +517,7 @@ int upload(T** p, const std::vector<T>& v) {
 void batch_free(csrk_batch* b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     for (void* p : {(void*)b->d_mats_user, (void*)b->d_mats_pq, (void*)b->d_mats_xr, (void*)b->d_tiles,
-                    (void*)b->d_counters, (void*)b->d_chunks, (void*)b->d_sys_mat, (void*)b->d_sys_col,
+                    (void*)b->d_items, (void*)b->d_itiles, (void*)b->d_status, (void*)b->d_counters, (void*)b->d_chunks, (void*)b->d_sys_mat, (void*)b->d_sys_col,
                     (void*)b->d_sys_off, (void*)b->d_mat_chunk0, (void*)b->d_mat_chunk1, (void*)b->d_moff,
                     (void*)b->d_mlen, (void*)b->B, (void*)b->X, (void*)b->R, (void*)b->P, (void*)b->Q,
                     (void*)b->partials, (void*)b->st, (void*)b->d_true, (void*)b->d_ptrs_in,
@@ -326,9 +529,18 @@ void batch_free(csrk_batch* b) {
 
 int launch_batch_spmm(csrk_batch* b, const BatchMat* table, double alpha, double beta, cudaStream_t s) {
     const int epi = (alpha != 1.0 ? csrk::dev::EPI_SCALE : 0) | (beta != 0.0 ? csrk::dev::EPI_ACCUM : 0);
-    const int grid = std::min<int>(b->ntiles, std::max(1, b->num_sms * 4));
-    if (grid == 0) return CSRK_OK;
-    batch_spmm_kernel<<<grid, BW * 32, 0, s>>>(table, b->d_tiles, b->ntiles, b->d_counters, alpha, beta, epi);
+    if (b->stages >= 2) {
+        const int grid = std::min<int>(b->nitiles, std::max(1, b->num_sms * 2));
+        if (grid == 0) return CSRK_OK;
+        const size_t smem = HDR_BYTES + (size_t)b->stages * b->stage_bytes;
+        batch_spmm_tma_kernel<<<grid, (TW + 1) * 32, smem, s>>>(table, b->d_items, b->d_itiles, b->nitiles,
+                                                                b->d_counters, alpha, beta, epi, b->stage_bytes,
+                                                                b->stages, b->timeout_ns, b->d_status);
+    } else {
+        const int grid = std::min<int>(b->ntiles, std::max(1, b->num_sms * 4));
+        if (grid == 0) return CSRK_OK;
+        batch_spmm_kernel<<<grid, BW * 32, 0, s>>>(table, b->d_tiles, b->ntiles, b->d_counters, alpha, beta, epi);
+    }
     CK_CUDA(cudaGetLastError(), "batch SpMM launch");
     return CSRK_OK;
 }
@@ -365,6 +577,12 @@ int csrk_batch_create(const csrk_handle* hs, int32_t count, const int32_t* k, cs
         cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, dev);
         std::vector<BatchTile> tiles;
         std::vector<double> weight;
+        std::vector<BatchItem> items;
+        std::vector<ItemTile> itiles;
+        std::vector<int32_t> itile_mat;
+        int64_t max_stage = 0;
+        int64_t item_bytes = ITEM_BYTES_DEFAULT;
+        if (const char* e = std::getenv("CSRK_BATCH_ITEM_BYTES")) item_bytes = std::max<int64_t>(1, std::atoll(e));
         std::vector<Chunk> chunks;
         std::vector<int32_t> sys_mat, sys_col, sys_off(count), mc0(count), mc1(count);
         std::vector<int64_t> moff(count), mlen(count);
@@ -396,6 +614,35 @@ int csrk_batch_create(const csrk_handle* hs, int32_t count, const int32_t* k, cs
                     weight.push_back((double)acc * (k[i] == 1 ? 1.0 : 0.5 + 0.5 * k[i]));
                     t0 = t + 1;
                     acc = 0;
+                }
+            }
+            // items: runs of whole super-rows with at most item_bytes of staged data (at
+            // least one super-row each), in tiles of ITEMS_PER_TILE
+            {
+                const int esz = val_bytes_of(m.vt);
+                const std::vector<int32_t>& srp = h->sr_ptr;
+                const std::vector<int32_t>& rp = h->m.rowptr;
+                const int32_t nsr = (int32_t)srp.size() - 1;
+                auto staged = [&](int32_t r0, int32_t r1) {
+                    int64_t a;
+                    uint32_t b1, b2, b3;
+                    slice16_rt(r0, (int64_t)r1 + 1, 4, a, b1);
+                    slice16_rt(rp[r0], rp[r1], 4, a, b2);
+                    slice16_rt(rp[r0], rp[r1], esz, a, b3);
+                    return (int64_t)b1 + b2 + b3;
+                };
+                const size_t first = items.size();
+                for (int32_t s0 = 0; s0 < nsr;) {
+                    int32_t s1 = s0 + 1;
+                    while (s1 < nsr && staged(srp[s0], srp[s1 + 1]) <= item_bytes) ++s1;
+                    const int32_t r0 = srp[s0], r1 = srp[s1];
+                    items.push_back({i, r0, r1, rp[r0], rp[r1], 0, 0, 0});
+                    max_stage = std::max(max_stage, staged(r0, r1));
+                    s0 = s1;
+                }
+                for (size_t q = first; q < items.size(); q += ITEMS_PER_TILE) {
+                    itiles.push_back({(int32_t)q, (int32_t)std::min(items.size(), q + ITEMS_PER_TILE)});
+                    itile_mat.push_back(i);
                 }
             }
             // vector chunks of about 8K elements (whole rows)
@@ -432,6 +679,40 @@ int csrk_batch_create(const csrk_handle* hs, int32_t count, const int32_t* k, cs
             });
             std::vector<BatchTile> sorted;
             for (size_t q : order) sorted.push_back(tiles[q]);
+            // the staged kernel's tiles in the same matrix order (stable: row order within)
+            std::vector<size_t> iorder(itiles.size());
+            std::iota(iorder.begin(), iorder.end(), 0);
+            std::stable_sort(iorder.begin(), iorder.end(), [&](size_t a, size_t c) {
+                const int32_t ma = itile_mat[a], mc = itile_mat[c];
+                if (ma == mc) return false;
+                if (mwork[ma] != mwork[mc]) return mwork[ma] > mwork[mc];
+                return ma < mc;
+            });
+            std::vector<ItemTile> isorted;
+            for (size_t q : iorder) isorted.push_back(itiles[q]);
+            b->nitems = (int32_t)items.size();
+            b->nitiles = (int32_t)isorted.size();
+            // stage plan: two blocks per SM, 2..16 stages of the largest item
+            int smem_sm = 0, optin = 0;
+            cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+            cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+            const int64_t budget = std::min<int64_t>(smem_sm / 2 - 1024, optin);
+            const int64_t stage = (max_stage + 127) & ~int64_t(127);
+            const int64_t fit = stage > 0 ? (budget - HDR_BYTES) / stage : 0;
+            if (fit >= 2 && stage <= (int64_t)UINT32_MAX) {
+                b->stage_bytes = (uint32_t)stage;
+                b->stages = (int32_t)std::min<int64_t>(fit, MAX_STAGES);
+                // the device maximum, not this batch's need: a later batch with smaller
+                // stages must not lower the limit under an earlier one
+                if (cudaFuncSetAttribute(batch_spmm_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) !=
+                    cudaSuccess)
+                    rc = fail(CSRK_ERR_CUDA, "batch kernel shared-memory attribute");
+            }
+            if (!rc) rc = upload(&b->d_items, items);
+            if (!rc) rc = upload(&b->d_itiles, isorted);
+            if (!rc) rc = dmalloc(&b->d_status, 1);
+            if (!rc && cudaMemset(b->d_status, 0, sizeof(int32_t)) != cudaSuccess)
+                rc = fail(CSRK_ERR_CUDA, "batch status word");
             b->ntiles = (int32_t)sorted.size();
             b->nchunks = (int32_t)chunks.size();
             b->nsys = (int32_t)sys_mat.size();
@@ -591,8 +872,22 @@ int csrk_batch_info(csrk_batch_handle b, int32_t* nmat, int32_t* nsys, int32_t* 
     if (!b) return fail(CSRK_ERR_ARG, "NULL batch");
     if (nmat) *nmat = b->nmat;
     if (nsys) *nsys = b->nsys;
-    if (ntiles) *ntiles = b->ntiles;
+    if (ntiles) *ntiles = b->stages >= 2 ? b->nitiles : b->ntiles;
     if (total) *total = b->total;
+    return CSRK_OK;
+}
+
+int csrk_batch_plan(csrk_batch_handle b, int32_t* items, int32_t* stages, int32_t* stage_bytes) {
+    if (!b) return fail(CSRK_ERR_ARG, "NULL batch");
+    if (items) *items = b->stages >= 2 ? b->nitems : 0;
+    if (stages) *stages = b->stages;
+    if (stage_bytes) *stage_bytes = (int32_t)b->stage_bytes;
+    return CSRK_OK;
+}
+
+int csrk_batch_device_status(csrk_batch_handle b, int32_t* status) {
+    if (!b || !status) return fail(CSRK_ERR_ARG, "NULL argument");
+    CK_CUDA(cudaMemcpy(status, b->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost), "read batch status");
     return CSRK_OK;
 }
 

@@ -62,6 +62,8 @@ _PROTOS = {
     "csrk_batch_spmm": [_vp, _d, _vp, _d, _vp, _u, _vp],
     "csrk_batch_cg": [_vp, _vp, _vp, _i32, _d, _vp, _vp, _vp],
     "csrk_batch_info": [_vp, _pi32, _pi32, _pi32, _pi64],
+    "csrk_batch_plan": [_vp, _pi32, _pi32, _pi32],
+    "csrk_batch_device_status": [_vp, _pi32],
     "csrk_batch_destroy": [_vp],
     "csrk_spmv_static_scratch": [_i32, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _d, _vp, _d, _vp, _vp],
 }
@@ -264,6 +266,18 @@ def batch_info(b):
     t = ctypes.c_int64()
     _check(lib().csrk_batch_info(b, *[ctypes.byref(x) for x in v], ctypes.byref(t)), "csrk_batch_info")
     return dict(nmat=v[0].value, nsys=v[1].value, ntiles=v[2].value, total=t.value)
+
+
+def batch_plan(b):
+    v = [ctypes.c_int32() for _ in range(3)]
+    _check(lib().csrk_batch_plan(b, *[ctypes.byref(x) for x in v]), "csrk_batch_plan")
+    return dict(items=v[0].value, stages=v[1].value, stage_bytes=v[2].value)
+
+
+def batch_device_status(b):
+    v = ctypes.c_int32()
+    _check(lib().csrk_batch_device_status(b, ctypes.byref(v)), "csrk_batch_device_status")
+    return v.value
 
 
 def batch_cg(b, Bs, Xs, iters, rtol=1e-10, stream=None):

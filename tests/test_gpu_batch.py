@@ -46,12 +46,30 @@ SPECS = [
 ]
 
 
-def test_batch_spmm_matches_oracle_and_replays():
+# item budgets: the default (16 KB), one super-row per item (many small stages), and a
+# budget so large that two stages cannot fit and the direct-load kernel runs
+ITEM_BUDGETS = {"default": None, "one_sr_per_item": "1", "direct": str(1 << 30)}
+
+
+@pytest.mark.parametrize("budget", list(ITEM_BUDGETS))
+def test_batch_spmm_matches_oracle_and_replays(budget, monkeypatch):
+    if ITEM_BUDGETS[budget] is None:
+        monkeypatch.delenv("CSRK_BATCH_ITEM_BYTES", raising=False)
+    else:
+        monkeypatch.setenv("CSRK_BATCH_ITEM_BYTES", ITEM_BUDGETS[budget])
     hs, forms = make_batch(SPECS)
     ks = [k for _, _, k, _ in SPECS]
     b = csrk.batch_create(hs, ks)
     info = csrk.batch_info(b)
     assert info["nmat"] == len(SPECS) and info["nsys"] == sum(ks)
+    plan = csrk.batch_plan(b)
+    if budget == "direct":
+        assert plan["stages"] == 0 and plan["items"] == 0
+    else:
+        assert 2 <= plan["stages"] <= 16 and plan["items"] >= len(SPECS)
+    if budget == "one_sr_per_item":
+        nsr = sum(csrk.info(h)["nsr"] for h in hs)
+        assert plan["items"] == nsr
     Xs, Ys, Y0s = [], [], []
     for i, (a, _, k, _) in enumerate(SPECS):
         X = synth.uniform_block(a.n, k, 100 + i)
@@ -78,6 +96,36 @@ def test_batch_spmm_matches_oracle_and_replays():
     (rp, ci, v), (a, _, k, _) = forms[0], SPECS[0]
     ref = ospmv.csr_spmm(a.n, rp, ci, v, Xs[0].cpu().numpy())
     assert np.allclose(Zs[0].cpu().numpy(), ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+    assert csrk.batch_device_status(b) == 0
+    csrk.batch_destroy(b)
+    for h in hs:
+        csrk.destroy(h)
+
+
+def test_batch_spmm_many_items_per_block():
+    """Enough items that every block's stage ring wraps many times (sampled rows)."""
+    specs = [(synth.stencil_3d(64, 64, 64, 27, "random_dd", 21), "f64", 4, (32, 4)),
+             (synth.stencil_3d(80, 80, 80, 7, "random_dd", 22), "f32", 1, (32, 8)),
+             (synth.fem_like(40, 23), "f64", 8, (32, 2))]
+    hs, forms = make_batch(specs)
+    b = csrk.batch_create(hs, [k for _, _, k, _ in specs])
+    plan = csrk.batch_plan(b)
+    assert plan["stages"] >= 2 and plan["items"] > plan["stages"] * 304   # rings wrap
+    Xs = [torch.tensor(synth.uniform_block(a.n, k, 400 + i), device=DEV) for i, (a, _, k, _) in enumerate(specs)]
+    Ys = [torch.full_like(x, np.nan) for x in Xs]
+    for _ in range(2):
+        csrk.batch_spmm(b, 1.0, Xs, 0.0, Ys)
+    torch.cuda.synchronize()
+    assert csrk.batch_device_status(b) == 0
+    rng = np.random.default_rng(5)
+    for i, ((a, _, k, _), (rp, ci, v)) in enumerate(zip(specs, forms)):
+        rows = np.unique(np.concatenate([rng.integers(0, a.n, 3000), [0, a.n - 1]]))
+        X, got = Xs[i].cpu().numpy(), Ys[i].cpu().numpy()
+        for c in range(k):
+            ref = ospmv.csr_spmv_rows(rp, ci, v, X[:, c], rows)
+            s = ospmv.abs_row_scale(rp, ci, v, X[:, c], rows=rows)
+            assert np.all(np.abs(got[rows, c] - ref) <= 1e-12 * s), (i, c)
+        assert not np.isnan(got).any()
     csrk.batch_destroy(b)
     for h in hs:
         csrk.destroy(h)
