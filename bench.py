@@ -422,7 +422,8 @@ def run_ours(args, world, rank, local):
 def run_batch(args, dev, stream, peak):
     """64 stencil / FEM matrices, n log-uniform in [1e3, 1e6] (seed 6), FP64 and FP32 values,
     k in {1,2,4,8,16} right-hand sides; sizes from the autotuner; one persistent SpMM
-    launch per step, then 200 CG iterations recorded in one CUDA graph."""
+    launch per step, then 200 CG iterations recorded in one CUDA graph, then CG to a 1e-10
+    true residual with the FP64 operator, plain FP64 vs mixed precision."""
     import torch
     from paper_2203_05096_gb300 import csrk
     specs = synth.batch_specs()
@@ -479,6 +480,25 @@ def run_batch(args, dev, stream, peak):
     out["cg"] = {"iterations_in_graph": 200, "ms": round(c0.elapsed_time(c1), 3),
                  "converged_systems": int(np.sum(rel <= 1e-10)), "max_relres": float(np.max(rel)),
                  "median_iterations": float(np.median(its))}
+    # time to a 1e-10 true residual on every system, FP64 operator: plain FP64 CG vs mixed
+    # precision (FP32 / BF16 inner products, FP64 residual every 20 iterations)
+    solve = {}
+    for inner in ("f64", "f32", "bf16"):
+        Xs = [torch.zeros_like(x) for x in Bs]
+        rst = 1 if inner == "bf16" else 0     # BF16: restart p = r at every replacement
+        csrk.batch_cg_solve(b, Bs, Xs, rtol=1e-10, maxit=2000, inner=inner, restart=rst)   # records the graph
+        torch.cuda.synchronize()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        rc, rel, its, cycles = csrk.batch_cg_solve(b, Bs, Xs, rtol=1e-10, maxit=2000, inner=inner, restart=rst)
+        s1.record(stream)
+        torch.cuda.synchronize()
+        solve[inner] = {"ms": round(s0.elapsed_time(s1), 3), "converged_systems": int(np.sum(rel <= 1e-10)),
+                        "all_converged": rc == 0, "max_relres": float(np.max(rel)), "cycles": cycles,
+                        "median_iterations": float(np.median(its)), "max_iterations": int(np.max(its))}
+    for inner in ("f32", "bf16"):
+        solve[inner]["speedup_vs_f64"] = round(solve["f64"]["ms"] / solve[inner]["ms"], 3)
+    out["cg_solve"] = {"rtol": 1e-10, "replace_every": 20, "runs": solve}
     csrk.batch_destroy(b)
     for h in hs:
         csrk.destroy(h)

@@ -202,8 +202,9 @@ int csrk_cg(csrk_handle h, const double* b, double* x, double rtol, int32_t maxi
  *          value dtype; all on the current device
  *   k      right-hand sides per matrix, 1..64
  * Each matrix is cut into items, runs of whole super-rows holding at most 24 KB of
- * staged data (rowptr, colidx and value slices rounded out to 16 bytes; at least one
- * super-row each; the environment variable CSRK_BATCH_ITEM_BYTES overrides the 24 KB),
+ * staged data (rowptr, colidx and value slices rounded out to 16 bytes, counted with 8-byte
+ * values so that the FP64 operator of any matrix fits; at least one super-row each; the
+ * environment variable CSRK_BATCH_ITEM_BYTES overrides the 24 KB),
  * grouped four to a tile; tiles are queued matrix by matrix (matrices by decreasing work,
  * each matrix's tiles in row order).  When two stages of the largest item do not fit a
  * block's shared memory (half an SM), the batch uses a direct-load kernel over tiles of
@@ -240,6 +241,37 @@ int csrk_batch_spmm(csrk_batch_handle b, double alpha, const void* const* X, dou
 int csrk_batch_cg(csrk_batch_handle b, const double* const* B, double* const* X,
                   int32_t iters, double rtol, double* relres, int32_t* iters_done,
                   void* stream);
+
+/* csrk_batch_cg_solve: independent CG solves A_i x = b for every (matrix, right-hand side)
+ * of the batch to a relative residual, in FP64 or mixed precision -- the batched
+ * counterpart of csrk_cg.  The operator is each matrix's FP64 values (the handle's input
+ * values, whatever its stored dtype).
+ *   B, X          host arrays of count DEVICE pointers (n_i x k_i FP64 blocks, reordered
+ *                 numbering); X receives the solutions (x0 = 0)
+ *   rtol          a system has converged when ||b - A x|| <= rtol ||b||, A in FP64 (> 0)
+ *   maxit         iteration limit per system, rounded up to whole cycles
+ *   inner         CSRK_F64: plain FP64 CG, q = A p with FP64 values; a system whose
+ *                 recursive residual meets rtol stops and is verified at the cycle's end.
+ *                 CSRK_F32 / CSRK_BF16: mixed precision -- q = A_lo p32 with the values
+ *                 rounded to that precision, p rounded to FP32 and FP32 accumulation, while
+ *                 vectors, dot products, alpha and beta stay FP64; at every cycle's end
+ *                 r = b - A x in FP64 (reliable update); a system whose recursive residual
+ *                 passes rtol/2 waits for that check.  Needs the staged SpMM kernel.
+ *   replace_every iterations per cycle (one CUDA graph, recorded once and replayed); the
+ *                 true residual of every running system is computed at each cycle's end
+ *   restart       mixed mode: 0 keeps p across a replacement unless the recomputed residual
+ *                 exceeds twice the recursive one or the cycle diverged (recursive residual
+ *                 up tenfold: the system stops until the cycle's end); 1 always restarts p = r
+ *   relres        optional host array (sum k_i): last true relative residual per system
+ *   iters_done    optional host array (sum k_i): iterations per system
+ *   cycles        optional: cycles run (each reads one 4-byte counter back to the host)
+ * Systems are ordered by matrix, then column.  Returns CSRK_OK when every system
+ * converged, CSRK_ERR_NOT_CONVERGED otherwise (maxit reached or p.q <= 0), X holding the
+ * last iterates.  k_i must be a power of two <= 32.  Synchronous. */
+int csrk_batch_cg_solve(csrk_batch_handle b, const double* const* B, double* const* X,
+                        double rtol, int32_t maxit, int inner, int32_t replace_every,
+                        int restart, double* relres, int32_t* iters_done, int32_t* cycles,
+                        void* stream);
 
 /* csrk_batch_info: matrices, systems (sum of k_i), tiles, and elements of one
  * concatenated vector (sum of n_i k_i); any pointer may be NULL. */

@@ -24,6 +24,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
+#include <cstring>
 #include <new>
 #include <numeric>
 #include <vector>
@@ -41,9 +42,10 @@ struct BatchMat {
     const void* vals;
     const int32_t* sr_ptr;
     const SsrDesc* desc;
-    const double* X;
-    double* Y;
-    int32_t n, k, vt, pad;
+    const void* X;   // FP64 (xt = 0) or FP32 (xt = 1) n x k block
+    void* Y;
+    int32_t n, k, vt;
+    int32_t xt;      // 1: FP32 vectors and FP32 accumulation (FP32 / BF16 values only)
 };
 
 struct BatchTile {
@@ -65,10 +67,12 @@ __device__ __noinline__ void sr_rows(const BatchMat* m, int rb, int re, double a
                                      int lane) {
     using namespace csrk::dev;
     const VT* vals = static_cast<const VT*>(m->vals);
+    const double* X = static_cast<const double*>(m->X);
+    double* Y = static_cast<double*>(m->Y);
     if constexpr (G == 1)
-        spmv_rows<VT, double, double, 1, 8>(rb, re, m->rowptr, m->colidx, vals, m->X, m->Y, alpha, beta, epi, lane);
+        spmv_rows<VT, double, double, 1, 8>(rb, re, m->rowptr, m->colidx, vals, X, Y, alpha, beta, epi, lane);
     else
-        spmm_rows<VT, double, double, G, CPL>(rb, re, m->rowptr, m->colidx, vals, m->X, m->k, m->Y, m->k, m->k,
+        spmm_rows<VT, double, double, G, CPL>(rb, re, m->rowptr, m->colidx, vals, X, m->k, Y, m->k, m->k,
                                               alpha, beta, epi, lane);
 }
 
@@ -160,8 +164,8 @@ __device__ __forceinline__ int rows_per_pass(int k) {
 
 // The row groups first, first + TW, ... of a staged item for one (value type, k) class.
 // rp / col / vb point into the stage; out of line like sr_rows.
-template <typename VT, int G, int CPL>
-__device__ __noinline__ void item_rows(const double* X, double* Y, int k, int r0, int r1, int p0, int first,
+template <typename VT, typename XT, typename AT, int G, int CPL>
+__device__ __noinline__ void item_rows(const XT* X, XT* Y, int k, int r0, int r1, int p0, int first,
                                        const int32_t* rp, const int32_t* col, const unsigned char* vb,
                                        double alpha, double beta, int epi, int lane) {
     using namespace csrk::dev;
@@ -172,26 +176,28 @@ __device__ __noinline__ void item_rows(const double* X, double* Y, int k, int r0
     for (int g = first; g < ng; g += TW) {
         const int rb = r0 + g * RPP, re = min(rb + RPP, r1);
         if constexpr (G == 1)
-            spmv_rows<VT, double, double, 1, 8>(rb, re, rp, col, val, X, Y, alpha, beta, epi, lane);
+            spmv_rows<VT, XT, AT, 1, 8>(rb, re, rp, col, val, X, Y, alpha, beta, epi, lane);
         else
-            spmm_rows<VT, double, double, G, CPL>(rb, re, rp, col, val, X, k, Y, k, k, alpha, beta, epi, lane);
+            spmm_rows<VT, XT, AT, G, CPL>(rb, re, rp, col, val, X, k, Y, k, k, alpha, beta, epi, lane);
     }
 }
 
-template <typename VT>
+template <typename VT, typename XT, typename AT>
 __device__ __forceinline__ void item_dispatch(const BatchMat* m, int r0, int r1, int p0, int first,
                                               const int32_t* rp, const int32_t* col, const unsigned char* vb,
                                               double alpha, double beta, int epi, int lane) {
     const int k = m->k;
-    const double* X = m->X;
-    double* Y = m->Y;
-    if (k == 1) item_rows<VT, 1, 1>(X, Y, k, r0, r1, p0, first, rp, col, vb, alpha, beta, epi, lane);
-    else if (k == 2) item_rows<VT, 2, 1>(X, Y, k, r0, r1, p0, first, rp, col, vb, alpha, beta, epi, lane);
-    else if (k <= 4) item_rows<VT, 4, 1>(X, Y, k, r0, r1, p0, first, rp, col, vb, alpha, beta, epi, lane);
-    else if (k <= 8) item_rows<VT, 8, 1>(X, Y, k, r0, r1, p0, first, rp, col, vb, alpha, beta, epi, lane);
-    else if (k <= 16) item_rows<VT, 16, 1>(X, Y, k, r0, r1, p0, first, rp, col, vb, alpha, beta, epi, lane);
-    else if (k <= 32) item_rows<VT, 32, 1>(X, Y, k, r0, r1, p0, first, rp, col, vb, alpha, beta, epi, lane);
-    else item_rows<VT, 32, 2>(X, Y, k, r0, r1, p0, first, rp, col, vb, alpha, beta, epi, lane);
+    const XT* X = static_cast<const XT*>(m->X);
+    XT* Y = static_cast<XT*>(m->Y);
+#define CSRK_ITEM(G, CPL) item_rows<VT, XT, AT, G, CPL>(X, Y, k, r0, r1, p0, first, rp, col, vb, alpha, beta, epi, lane)
+    if (k == 1) CSRK_ITEM(1, 1);
+    else if (k == 2) CSRK_ITEM(2, 1);
+    else if (k <= 4) CSRK_ITEM(4, 1);
+    else if (k <= 8) CSRK_ITEM(8, 1);
+    else if (k <= 16) CSRK_ITEM(16, 1);
+    else if (k <= 32) CSRK_ITEM(32, 1);
+    else CSRK_ITEM(32, 2);
+#undef CSRK_ITEM
 }
 
 // At most 60 registers per thread: two blocks of 17 warps per SM.
@@ -302,9 +308,19 @@ __global__ void __launch_bounds__((TW + 1) * 32, 2)
             seq = (seq + ng) % TW;
             if (first < ng) {
                 const int vt = m->vt;
-                if (vt == csrk::VAL_F64) item_dispatch<double>(m, h.r0, h.r1, h.p0, first, rp, col, vb, alpha, beta, epi, lane);
-                else if (vt == csrk::VAL_F32) item_dispatch<float>(m, h.r0, h.r1, h.p0, first, rp, col, vb, alpha, beta, epi, lane);
-                else item_dispatch<bf16_t>(m, h.r0, h.r1, h.p0, first, rp, col, vb, alpha, beta, epi, lane);
+#define CSRK_DISPATCH(VT, XT, AT) \
+    item_dispatch<VT, XT, AT>(m, h.r0, h.r1, h.p0, first, rp, col, vb, alpha, beta, epi, lane)
+                if (m->xt) {   // FP32 vectors and accumulation: the inner product of a mixed solve
+                    if (vt == csrk::VAL_F32) CSRK_DISPATCH(float, float, float);
+                    else CSRK_DISPATCH(bf16_t, float, float);
+                } else if (vt == csrk::VAL_F64) {
+                    CSRK_DISPATCH(double, double, double);
+                } else if (vt == csrk::VAL_F32) {
+                    CSRK_DISPATCH(float, double, double);
+                } else {
+                    CSRK_DISPATCH(bf16_t, double, double);
+                }
+#undef CSRK_DISPATCH
             }
         }
         __syncwarp();
@@ -318,6 +334,13 @@ constexpr int VT_THREADS = 256;   // vector-kernel block; a multiple of every k 
 struct SysState {   // per (matrix, right-hand side)
     double rr, pq, alpha, beta, bb, tol2;
     int32_t frozen, iters;
+    // csrk_batch_cg_solve only
+    double rr_start;   // r.r at the start of the current cycle
+    double rr_true;    // last ||b - A64 x||^2
+    int32_t done;      // 1 converged (true residual), 2 breakdown (p.q <= 0)
+    int32_t replace;   // at the end of this cycle: r = the true residual
+    int32_t restart;   //                            p = r
+    int32_t pad;
 };
 
 // Per-chunk, per-column partial sums of a[i]*b[i] over the chunk's elements.  With k a
@@ -338,10 +361,10 @@ __device__ void chunk_partial(double v, int k, double* out /* k entries */) {
 
 __device__ __forceinline__ int sys_of(const int32_t* sys_off, int mat, int c) { return sys_off[mat] + c; }
 
-// B -> R, P; X = 0; partial b.b
+// B -> R, P (and its FP32 copy P32 when given); X = 0; partial b.b
 __global__ void __launch_bounds__(VT_THREADS) bcg_init(const Chunk* __restrict__ chunks, const BatchMat* mats,
                                                        const double* __restrict__ Bv, double* X, double* R,
-                                                       double* P, double* partials) {
+                                                       double* P, float* P32, double* partials) {
     const Chunk ch = chunks[blockIdx.x];
     const int k = mats[ch.mat].k;
     const int64_t e0 = ch.off, e1 = ch.off + (int64_t)(ch.row1 - ch.row0) * k;
@@ -351,27 +374,34 @@ __global__ void __launch_bounds__(VT_THREADS) bcg_init(const Chunk* __restrict__
         X[e] = 0.0;
         R[e] = b;
         P[e] = b;
+        if (P32) P32[e] = (float)b;
         v += b * b;
     }
     chunk_partial(v, k, partials + (int64_t)blockIdx.x * 32);
 }
 
+__device__ __forceinline__ double as_f64(double v) { return v; }
+__device__ __forceinline__ double as_f64(float v) { return (double)v; }
+
+// partial A.B per system; B is FP64 or the FP32 product of a mixed solve
+template <typename TB>
 __global__ void __launch_bounds__(VT_THREADS) bcg_dot(const Chunk* __restrict__ chunks, const BatchMat* mats,
-                                                      const double* __restrict__ A, const double* __restrict__ Bv,
+                                                      const double* __restrict__ A, const TB* __restrict__ Bv,
                                                       double* partials) {
     const Chunk ch = chunks[blockIdx.x];
     const int k = mats[ch.mat].k;
     const int64_t e0 = ch.off, e1 = ch.off + (int64_t)(ch.row1 - ch.row0) * k;
     double v = 0.0;
-    for (int64_t e = e0 + threadIdx.x; e < e1; e += VT_THREADS) v += A[e] * Bv[e];
+    for (int64_t e = e0 + threadIdx.x; e < e1; e += VT_THREADS) v += A[e] * as_f64(Bv[e]);
     chunk_partial(v, k, partials + (int64_t)blockIdx.x * 32);
 }
 
 // X += alpha P; R -= alpha Q; partial r.r
+template <typename TQ>
 __global__ void __launch_bounds__(VT_THREADS) bcg_update_xr(const Chunk* __restrict__ chunks, const BatchMat* mats,
                                                             const int32_t* sys_off, const SysState* st,
                                                             double* X, double* R, const double* __restrict__ P,
-                                                            const double* __restrict__ Q, double* partials) {
+                                                            const TQ* __restrict__ Q, double* partials) {
     const Chunk ch = chunks[blockIdx.x];
     const int k = mats[ch.mat].k;
     const int64_t e0 = ch.off, e1 = ch.off + (int64_t)(ch.row1 - ch.row0) * k;
@@ -379,30 +409,65 @@ __global__ void __launch_bounds__(VT_THREADS) bcg_update_xr(const Chunk* __restr
     double v = 0.0;
     for (int64_t e = e0 + threadIdx.x; e < e1; e += VT_THREADS) {
         X[e] += alpha * P[e];
-        const double r = R[e] - alpha * Q[e];
+        const double r = R[e] - alpha * as_f64(Q[e]);
         R[e] = r;
         v += r * r;
     }
     chunk_partial(v, k, partials + (int64_t)blockIdx.x * 32);
 }
 
-// P = R + beta P
+// P = R + beta P (and P32 = P rounded to FP32 when given)
 __global__ void __launch_bounds__(VT_THREADS) bcg_update_p(const Chunk* __restrict__ chunks, const BatchMat* mats,
                                                            const int32_t* sys_off, const SysState* st,
-                                                           const double* __restrict__ R, double* P) {
+                                                           const double* __restrict__ R, double* P, float* P32) {
     const Chunk ch = chunks[blockIdx.x];
     const int k = mats[ch.mat].k;
     const int64_t e0 = ch.off, e1 = ch.off + (int64_t)(ch.row1 - ch.row0) * k;
     const double beta = st[sys_of(sys_off, ch.mat, threadIdx.x % k)].beta;
-    for (int64_t e = e0 + threadIdx.x; e < e1; e += VT_THREADS) P[e] = R[e] + beta * P[e];
+    for (int64_t e = e0 + threadIdx.x; e < e1; e += VT_THREADS) {
+        const double p = R[e] + beta * P[e];
+        P[e] = p;
+        if (P32) P32[e] = (float)p;
+    }
+}
+
+// End of a cycle of csrk_batch_cg_solve: per system, R = T (the true residual) when its
+// `replace` flag is set, then P = R (and P32) when `restart` is set.
+__global__ void __launch_bounds__(VT_THREADS) bcg_replace(const Chunk* __restrict__ chunks, const BatchMat* mats,
+                                                          const int32_t* sys_off, const SysState* st,
+                                                          const double* __restrict__ T, double* R, double* P,
+                                                          float* P32) {
+    const Chunk ch = chunks[blockIdx.x];
+    const int k = mats[ch.mat].k;
+    const int64_t e0 = ch.off, e1 = ch.off + (int64_t)(ch.row1 - ch.row0) * k;
+    const SysState& y = st[sys_of(sys_off, ch.mat, threadIdx.x % k)];
+    const bool rep = y.replace, rst = y.restart;
+    if (!rep && !rst) return;
+    for (int64_t e = e0 + threadIdx.x; e < e1; e += VT_THREADS) {
+        const double r = rep ? T[e] : R[e];
+        if (rep) R[e] = r;
+        if (rst) {
+            P[e] = r;
+            if (P32) P32[e] = (float)r;
+        }
+    }
 }
 
 // One warp per system: sum the system's chunk partials in chunk order (lanes stride, then
 // a fixed shuffle tree), then apply `stage`:
-//   0: b.b (init)   1: p.q -> alpha   2: r.r -> beta, freeze when converged   3: true r.r
+//   0: b.b (init)   1: p.q -> alpha   2: r.r -> beta, freeze when r.r <= margin2 tol^2
+//   3: true r.r -> relative residual   4: true r.r at the end of a solve cycle -> converged,
+//   or (counted in *active) continue with r replaced / p restarted per the solve's rules
+struct FinalizeOpts {
+    double margin2;      // stage 2 freeze threshold, as a factor of tol^2
+    int32_t mixed;       // stage 4: mixed-precision rules (always replace r)
+    int32_t restart;     // stage 4, mixed: always restart p = r
+    int32_t* active;     // stage 4: count of systems still running
+};
+
 __global__ void bcg_finalize(const int32_t* sys_mat, const int32_t* sys_col, const int32_t* mat_chunk0,
                              const int32_t* mat_chunk1, const double* partials, SysState* st, int32_t nsys,
-                             int stage, double rtol, double* out_true) {
+                             int stage, double rtol, double* out_true, FinalizeOpts o) {
     const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (s >= nsys) return;
@@ -416,15 +481,23 @@ __global__ void bcg_finalize(const int32_t* sys_mat, const int32_t* sys_col, con
     if (stage == 0) {
         y.bb = t;
         y.rr = t;
+        y.rr_start = t;
+        y.rr_true = t;
         y.tol2 = rtol * rtol * t;
         y.frozen = (t == 0.0);
+        y.done = (t == 0.0);
+        y.replace = 0;
+        y.restart = 0;
         y.iters = 0;
         y.alpha = 0.0;
         y.beta = 0.0;
     } else if (stage == 1) {
         y.pq = t;
         y.alpha = (y.frozen || !(t > 0.0)) ? 0.0 : y.rr / t;
-        if (!(t > 0.0)) y.frozen = 1;
+        if (!y.frozen && !(t > 0.0)) {   // breakdown: the system stops for good
+            y.frozen = 1;
+            y.done = 2;
+        }
     } else if (stage == 2) {
         if (y.frozen) {
             y.beta = 0.0;
@@ -433,12 +506,38 @@ __global__ void bcg_finalize(const int32_t* sys_mat, const int32_t* sys_col, con
         y.beta = t / y.rr;
         y.rr = t;
         y.iters += 1;
-        if (t <= y.tol2) {
+        // stop until the cycle's end: converged by the recursion, or (mixed) diverging --
+        // the recursive residual up tenfold within the cycle
+        if (t <= o.margin2 * y.tol2 || (o.mixed && t > 100.0 * y.rr_start)) {
             y.frozen = 1;
             y.beta = 0.0;
         }
-    } else {
+    } else if (stage == 3) {
         out_true[s] = y.bb > 0.0 ? sqrt(t / y.bb) : 0.0;
+    } else {
+        y.replace = 0;
+        y.restart = 0;
+        if (y.done) return;
+        y.rr_true = t;
+        if (t <= y.tol2) {   // converged on the FP64 residual
+            y.done = 1;
+            y.frozen = 1;
+            y.beta = 0.0;
+            return;
+        }
+        atomicAdd(o.active, 1);
+        const bool pending = y.frozen;   // stopped early in the cycle, and not converged
+        if (o.mixed) {
+            y.replace = 1;
+            y.restart = o.restart || t > 4.0 * y.rr || y.rr > 100.0 * y.rr_start;
+            y.rr = t;
+        } else if (pending) {
+            y.replace = 1;
+            y.restart = 1;
+            y.rr = t;
+        }
+        y.frozen = 0;
+        y.rr_start = y.rr;
     }
 }
 
@@ -487,6 +586,18 @@ struct csrk_batch {
     BatchMat* h_pinned_mats = nullptr;
     // CG buffers
     double *B = nullptr, *X = nullptr, *R = nullptr, *P = nullptr, *Q = nullptr, *partials = nullptr;
+    // csrk_batch_cg_solve: FP32 copies of P and of the inner product, operator tables
+    // (inner FP64 P -> Q, inner low precision P32 -> Q32, true residual X -> Q), the
+    // running-system counter and its pinned host copy, the per-cycle graph
+    float *P32 = nullptr, *Q32 = nullptr;
+    BatchMat* d_mats_pq64 = nullptr;
+    BatchMat* d_mats_lo = nullptr;
+    BatchMat* d_mats_t64 = nullptr;
+    int lo_vt = -1;
+    int32_t* d_active = nullptr;
+    int32_t* h_active = nullptr;
+    cudaGraphExec_t sexec = nullptr;
+    int sexec_key[3] = {-1, -1, -1};   // inner, replace_every, restart
     SysState* st = nullptr;
     double* d_true = nullptr;
     const double** d_ptrs_in = nullptr;
@@ -516,6 +627,11 @@ int upload(T** p, const std::vector<T>& v) {
 
 void batch_free(csrk_batch* b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->sexec) cudaGraphExecDestroy(b->sexec);
+    for (void* p : {(void*)b->P32, (void*)b->Q32, (void*)b->d_mats_pq64, (void*)b->d_mats_lo,
+                    (void*)b->d_mats_t64, (void*)b->d_active})
+        cudaFree(p);
+    if (b->h_active) cudaFreeHost(b->h_active);
     for (void* p : {(void*)b->d_mats_user, (void*)b->d_mats_pq, (void*)b->d_mats_xr, (void*)b->d_tiles,
                     (void*)b->d_items, (void*)b->d_itiles, (void*)b->d_status, (void*)b->d_counters, (void*)b->d_chunks, (void*)b->d_sys_mat, (void*)b->d_sys_col,
                     (void*)b->d_sys_off, (void*)b->d_mat_chunk0, (void*)b->d_mat_chunk1, (void*)b->d_moff,
@@ -545,12 +661,23 @@ int launch_batch_spmm(csrk_batch* b, const BatchMat* table, double alpha, double
     return CSRK_OK;
 }
 
-int fill_table(csrk_batch* b, BatchMat* table, const double* xbase, double* ybase) {
+// A device table binding matrix i to the concatenated vectors at xbase / ybase (element
+// offset sum_{j<i} n_j k_j), with value type vt (-1: each handle's stored type) and
+// FP32 vectors when xt = 1.
+int fill_table(csrk_batch* b, BatchMat* table, const void* xbase, void* ybase, int vt = -1, int xt = 0) {
     std::vector<BatchMat> t = b->h_mats;
+    const size_t esz = xt ? sizeof(float) : sizeof(double);
     int64_t off = 0;
     for (int32_t i = 0; i < b->nmat; ++i) {
-        t[i].X = xbase + off;
-        t[i].Y = ybase + off;
+        if (vt >= 0) {
+            int rc = ensure_vals(b->hs[i], vt);
+            if (rc) return rc;
+            t[i].vals = b->hs[i]->d_vals[vt];
+            t[i].vt = vt;
+        }
+        t[i].xt = xt;
+        t[i].X = static_cast<const unsigned char*>(xbase) + off * esz;
+        t[i].Y = static_cast<unsigned char*>(ybase) + off * esz;
         off += (int64_t)t[i].n * t[i].k;
     }
     CK_CUDA(cudaMemcpy(table, t.data(), t.size() * sizeof(BatchMat), cudaMemcpyHostToDevice), "batch table");
@@ -619,7 +746,7 @@ int csrk_batch_create(const csrk_handle* hs, int32_t count, const int32_t* k, cs
             // items: runs of whole super-rows with at most item_bytes of staged data (at
             // least one super-row each), in tiles of ITEMS_PER_TILE
             {
-                const int esz = val_bytes_of(m.vt);
+                const int esz = 8;   // sized for FP64 values, so every operator of a solve fits a stage
                 const std::vector<int32_t>& srp = h->sr_ptr;
                 const std::vector<int32_t>& rp = h->m.rowptr;
                 const int32_t nsr = (int32_t)srp.size() - 1;
@@ -763,8 +890,8 @@ int csrk_batch_spmm(csrk_batch_handle b, double alpha, const void* const* X, dou
         for (int32_t i = 0; i < b->nmat; ++i) {
             if (!X[i] || !Y[i] || X[i] == Y[i]) return fail(CSRK_ERR_ARG, "bad vector pointer");
             b->h_pinned_mats[i] = b->h_mats[i];
-            b->h_pinned_mats[i].X = static_cast<const double*>(X[i]);
-            b->h_pinned_mats[i].Y = static_cast<double*>(Y[i]);
+            b->h_pinned_mats[i].X = X[i];
+            b->h_pinned_mats[i].Y = Y[i];
         }
         CK_CUDA(cudaMemcpyAsync(b->d_mats_user, b->h_pinned_mats, b->nmat * sizeof(BatchMat),
                                 cudaMemcpyHostToDevice, s), "bind vectors");
@@ -774,22 +901,104 @@ int csrk_batch_spmm(csrk_batch_handle b, double alpha, const void* const* X, dou
     return launch_batch_spmm(b, b->d_mats_user, alpha, beta, s);
 }
 
-static int bcg_enqueue_iteration(csrk_batch* b, cudaStream_t s) {
-    const int gv = b->nchunks;
+}  // extern "C"
+
+namespace {
+
+void bcg_fin(csrk_batch* b, cudaStream_t s, int stage, double rtol = 0.0, double* out = nullptr,
+                    FinalizeOpts o = FinalizeOpts{1.0, 0, 0, nullptr}) {
     const int fin_blocks = (b->nsys * 32 + 255) / 256;
+    bcg_finalize<<<fin_blocks, 256, 0, s>>>(b->d_sys_mat, b->d_sys_col, b->d_mat_chunk0, b->d_mat_chunk1,
+                                            b->partials, b->st, b->nsys, stage, rtol, out, o);
+}
+
+int bcg_enqueue_iteration(csrk_batch* b, cudaStream_t s) {
+    const int gv = b->nchunks;
     int rc;
     if ((rc = launch_batch_spmm(b, b->d_mats_pq, 1.0, 0.0, s))) return rc;   // Q = A P
-    bcg_dot<<<gv, VT_THREADS, 0, s>>>(b->d_chunks, b->d_mats_pq, b->P, b->Q, b->partials);
-    bcg_finalize<<<fin_blocks, 256, 0, s>>>(b->d_sys_mat, b->d_sys_col, b->d_mat_chunk0, b->d_mat_chunk1,
-                                            b->partials, b->st, b->nsys, 1, 0.0, nullptr);
-    bcg_update_xr<<<gv, VT_THREADS, 0, s>>>(b->d_chunks, b->d_mats_pq, b->d_sys_off, b->st, b->X, b->R, b->P,
-                                            b->Q, b->partials);
-    bcg_finalize<<<fin_blocks, 256, 0, s>>>(b->d_sys_mat, b->d_sys_col, b->d_mat_chunk0, b->d_mat_chunk1,
-                                            b->partials, b->st, b->nsys, 2, 0.0, nullptr);
-    bcg_update_p<<<gv, VT_THREADS, 0, s>>>(b->d_chunks, b->d_mats_pq, b->d_sys_off, b->st, b->R, b->P);
+    bcg_dot<double><<<gv, VT_THREADS, 0, s>>>(b->d_chunks, b->d_mats_pq, b->P, b->Q, b->partials);
+    bcg_fin(b, s, 1);
+    bcg_update_xr<double><<<gv, VT_THREADS, 0, s>>>(b->d_chunks, b->d_mats_pq, b->d_sys_off, b->st, b->X, b->R,
+                                                    b->P, b->Q, b->partials);
+    bcg_fin(b, s, 2);
+    bcg_update_p<<<gv, VT_THREADS, 0, s>>>(b->d_chunks, b->d_mats_pq, b->d_sys_off, b->st, b->R, b->P, nullptr);
     CK_CUDA(cudaGetLastError(), "batched CG launch");
     return CSRK_OK;
 }
+
+// One cycle of csrk_batch_cg_solve: E iterations, then the true residual T = B - A64 X
+// (into Q), the per-system decision, and r / p replacement where decided.
+int bsolve_enqueue_cycle(csrk_batch* b, cudaStream_t s, bool mixed, int32_t E, int restart) {
+    const int gv = b->nchunks;
+    const FinalizeOpts o2{mixed ? 0.25 : 1.0, mixed ? 1 : 0, 0, nullptr};   // mixed: stop at rtol/2, then verify
+    int rc;
+    CK_CUDA(cudaMemsetAsync(b->d_active, 0, sizeof(int32_t), s), "reset counter");
+    for (int32_t it = 0; it < E; ++it) {
+        if (mixed) {
+            if ((rc = launch_batch_spmm(b, b->d_mats_lo, 1.0, 0.0, s))) return rc;   // Q32 = A_lo P32
+            bcg_dot<float><<<gv, VT_THREADS, 0, s>>>(b->d_chunks, b->d_mats_pq, b->P, b->Q32, b->partials);
+            bcg_fin(b, s, 1);
+            bcg_update_xr<float><<<gv, VT_THREADS, 0, s>>>(b->d_chunks, b->d_mats_pq, b->d_sys_off, b->st, b->X,
+                                                           b->R, b->P, b->Q32, b->partials);
+        } else {
+            if ((rc = launch_batch_spmm(b, b->d_mats_pq64, 1.0, 0.0, s))) return rc;   // Q = A64 P
+            bcg_dot<double><<<gv, VT_THREADS, 0, s>>>(b->d_chunks, b->d_mats_pq, b->P, b->Q, b->partials);
+            bcg_fin(b, s, 1);
+            bcg_update_xr<double><<<gv, VT_THREADS, 0, s>>>(b->d_chunks, b->d_mats_pq, b->d_sys_off, b->st, b->X,
+                                                            b->R, b->P, b->Q, b->partials);
+        }
+        bcg_fin(b, s, 2, 0.0, nullptr, o2);
+        bcg_update_p<<<gv, VT_THREADS, 0, s>>>(b->d_chunks, b->d_mats_pq, b->d_sys_off, b->st, b->R, b->P,
+                                               mixed ? b->P32 : nullptr);
+    }
+    CK_CUDA(cudaMemcpyAsync(b->Q, b->B, (size_t)b->total * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy B");
+    if ((rc = launch_batch_spmm(b, b->d_mats_t64, -1.0, 1.0, s))) return rc;   // Q = B - A64 X
+    bcg_dot<double><<<gv, VT_THREADS, 0, s>>>(b->d_chunks, b->d_mats_pq, b->Q, b->Q, b->partials);
+    bcg_fin(b, s, 4, 0.0, nullptr, FinalizeOpts{1.0, mixed ? 1 : 0, restart, b->d_active});
+    bcg_replace<<<gv, VT_THREADS, 0, s>>>(b->d_chunks, b->d_mats_pq, b->d_sys_off, b->st, b->Q, b->R, b->P,
+                                          mixed ? b->P32 : nullptr);
+    CK_CUDA(cudaGetLastError(), "batched CG cycle");
+    return CSRK_OK;
+}
+
+// CG workspace shared by csrk_batch_cg and csrk_batch_cg_solve.
+int bcg_workspace(csrk_batch* b) {
+    if (b->B) return CSRK_OK;
+    const size_t tot = (size_t)b->total;
+    int rc;
+    if ((rc = dmalloc(&b->B, tot)) || (rc = dmalloc(&b->X, tot)) || (rc = dmalloc(&b->R, tot)) ||
+        (rc = dmalloc(&b->P, tot)) || (rc = dmalloc(&b->Q, tot)) ||
+        (rc = dmalloc(&b->partials, (size_t)b->nchunks * 32)) || (rc = dmalloc(&b->st, (size_t)b->nsys)) ||
+        (rc = dmalloc(&b->d_true, (size_t)b->nsys)) || (rc = dmalloc(&b->d_ptrs_in, (size_t)b->nmat)) ||
+        (rc = dmalloc(&b->d_ptrs_out, (size_t)b->nmat)))
+        return rc;
+    if ((rc = fill_table(b, b->d_mats_pq, b->P, b->Q)) || (rc = fill_table(b, b->d_mats_xr, b->X, b->R)))
+        return rc;
+    CK_CUDA(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking), "batch stream");
+    return CSRK_OK;
+}
+
+// Record `enqueue` on the capture stream into a graph and instantiate it.
+template <typename F>
+int bcg_capture(csrk_batch* b, cudaGraphExec_t* exec, F enqueue) {
+    CK_CUDA(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
+    int rc = enqueue(b->cap);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(b->cap, &graph);
+    if (rc) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "end capture");
+    e = cudaGraphInstantiate(exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
+    return CSRK_OK;
+}
+
+}  // namespace
+
+extern "C" {
 
 int csrk_batch_cg(csrk_batch_handle b, const double* const* B, double* const* Xout, int32_t iters,
                   double rtol, double* relres, int32_t* iters_done, void* stream) {
@@ -800,26 +1009,14 @@ int csrk_batch_cg(csrk_batch_handle b, const double* const* B, double* const* Xo
     }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     int rc;
-    if (!b->B) {
-        const size_t tot = (size_t)b->total;
-        if ((rc = dmalloc(&b->B, tot)) || (rc = dmalloc(&b->X, tot)) || (rc = dmalloc(&b->R, tot)) ||
-            (rc = dmalloc(&b->P, tot)) || (rc = dmalloc(&b->Q, tot)) ||
-            (rc = dmalloc(&b->partials, (size_t)b->nchunks * 32)) || (rc = dmalloc(&b->st, (size_t)b->nsys)) ||
-            (rc = dmalloc(&b->d_true, (size_t)b->nsys)) || (rc = dmalloc(&b->d_ptrs_in, (size_t)b->nmat)) ||
-            (rc = dmalloc(&b->d_ptrs_out, (size_t)b->nmat)))
-            return rc;
-        if ((rc = fill_table(b, b->d_mats_pq, b->P, b->Q)) || (rc = fill_table(b, b->d_mats_xr, b->X, b->R)))
-            return rc;
-        CK_CUDA(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking), "batch stream");
-    }
+    if ((rc = bcg_workspace(b))) return rc;
     CK_CUDA(cudaMemcpyAsync(b->d_ptrs_in, B, b->nmat * sizeof(double*), cudaMemcpyHostToDevice, s), "B pointers");
     CK_CUDA(cudaMemcpyAsync(b->d_ptrs_out, Xout, b->nmat * sizeof(double*), cudaMemcpyHostToDevice, s), "X pointers");
     const dim3 cg_grid(64, std::min<int32_t>(b->nmat, 65535));
     bcg_gather<<<cg_grid, 256, 0, s>>>(b->d_ptrs_in, b->d_moff, b->d_mlen, b->nmat, b->B);
-    const int fin_blocks = (b->nsys * 32 + 255) / 256;
-    bcg_init<<<b->nchunks, VT_THREADS, 0, s>>>(b->d_chunks, b->d_mats_pq, b->B, b->X, b->R, b->P, b->partials);
-    bcg_finalize<<<fin_blocks, 256, 0, s>>>(b->d_sys_mat, b->d_sys_col, b->d_mat_chunk0, b->d_mat_chunk1,
-                                            b->partials, b->st, b->nsys, 0, rtol, nullptr);
+    bcg_init<<<b->nchunks, VT_THREADS, 0, s>>>(b->d_chunks, b->d_mats_pq, b->B, b->X, b->R, b->P, nullptr,
+                                               b->partials);
+    bcg_fin(b, s, 0, rtol);
     CK_CUDA(cudaGetLastError(), "batched CG init");
     if (!b->exec || b->exec_iters != iters) {
         if (b->exec) {
@@ -827,27 +1024,20 @@ int csrk_batch_cg(csrk_batch_handle b, const double* const* B, double* const* Xo
             b->exec = nullptr;
         }
         CK_CUDA(cudaStreamSynchronize(s), "synchronise");
-        CK_CUDA(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
-        for (int32_t it = 0; it < iters && !rc; ++it) rc = bcg_enqueue_iteration(b, b->cap);
-        cudaGraph_t graph = nullptr;
-        cudaError_t e = cudaStreamEndCapture(b->cap, &graph);
-        if (rc) {
-            if (graph) cudaGraphDestroy(graph);
-            return rc;
-        }
-        if (e != cudaSuccess) return cuda_fail(e, "end capture");
-        e = cudaGraphInstantiate(&b->exec, graph, 0);
-        cudaGraphDestroy(graph);
-        if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
+        rc = bcg_capture(b, &b->exec, [&](cudaStream_t cs) {
+            int r = CSRK_OK;
+            for (int32_t it = 0; it < iters && !r; ++it) r = bcg_enqueue_iteration(b, cs);
+            return r;
+        });
+        if (rc) return rc;
         b->exec_iters = iters;
     }
     CK_CUDA(cudaGraphLaunch(b->exec, s), "graph launch");
     // true residuals: R = B - A X, then per-system norms
     CK_CUDA(cudaMemcpyAsync(b->R, b->B, (size_t)b->total * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy B");
     if ((rc = launch_batch_spmm(b, b->d_mats_xr, -1.0, 1.0, s))) return rc;   // R = B - A X
-    bcg_dot<<<b->nchunks, VT_THREADS, 0, s>>>(b->d_chunks, b->d_mats_pq, b->R, b->R, b->partials);
-    bcg_finalize<<<fin_blocks, 256, 0, s>>>(b->d_sys_mat, b->d_sys_col, b->d_mat_chunk0, b->d_mat_chunk1,
-                                            b->partials, b->st, b->nsys, 3, 0.0, b->d_true);
+    bcg_dot<double><<<b->nchunks, VT_THREADS, 0, s>>>(b->d_chunks, b->d_mats_pq, b->R, b->R, b->partials);
+    bcg_fin(b, s, 3, 0.0, b->d_true);
     bcg_scatter<<<cg_grid, 256, 0, s>>>(b->X, b->d_moff, b->d_mlen, b->nmat, b->d_ptrs_out);
     CK_CUDA(cudaGetLastError(), "batched CG finish");
     std::vector<SysState> hs(b->nsys);
@@ -857,6 +1047,91 @@ int csrk_batch_cg(csrk_batch_handle b, const double* const* B, double* const* Xo
     CK_CUDA(cudaStreamSynchronize(s), "synchronise");
     if (iters_done)
         for (int32_t q = 0; q < b->nsys; ++q) iters_done[q] = hs[q].iters;
+    return CSRK_OK;
+}
+
+int csrk_batch_cg_solve(csrk_batch_handle b, const double* const* B, double* const* Xout, double rtol,
+                        int32_t maxit, int inner, int32_t replace_every, int restart, double* relres,
+                        int32_t* iters_done, int32_t* cycles_out, void* stream) {
+    if (!b || !B || !Xout || maxit < 1 || !(rtol > 0.0) || replace_every < 1 || (restart != 0 && restart != 1))
+        return fail(CSRK_ERR_ARG, "bad batched CG arguments");
+    if (inner != CSRK_F64 && inner != CSRK_F32 && inner != CSRK_BF16)
+        return fail(CSRK_ERR_ARG, "inner must be CSRK_F64, CSRK_F32 or CSRK_BF16");
+    for (int32_t i = 0; i < b->nmat; ++i) {
+        const int k = b->k[i];
+        if (k & (k - 1) || k > 32) return fail(CSRK_ERR_UNSUPPORTED, "batched CG takes k in {1,2,4,8,16,32}");
+    }
+    const bool mixed = inner != CSRK_F64;
+    if (mixed && b->stages < 2)
+        return fail(CSRK_ERR_UNSUPPORTED, "mixed-precision batched CG needs the staged SpMM kernel "
+                                          "(super-rows too large for two shared-memory stages)");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int rc;
+    if ((rc = bcg_workspace(b))) return rc;
+    if (!b->d_mats_t64) {   // FP64 operator tables: inner P -> Q, true residual X -> Q
+        if ((rc = dmalloc(&b->d_mats_pq64, b->nmat)) || (rc = dmalloc(&b->d_mats_t64, b->nmat)) ||
+            (rc = dmalloc(&b->d_active, 1)))
+            return rc;
+        if (cudaMallocHost(&b->h_active, sizeof(int32_t)) != cudaSuccess)
+            return fail(CSRK_ERR_ALLOC, "pinned counter");
+        if ((rc = fill_table(b, b->d_mats_pq64, b->P, b->Q, csrk::VAL_F64)) ||
+            (rc = fill_table(b, b->d_mats_t64, b->X, b->Q, csrk::VAL_F64)))
+            return rc;
+    }
+    if (mixed) {
+        const int lo = inner == CSRK_F32 ? csrk::VAL_F32 : csrk::VAL_BF16;
+        if (!b->P32) {
+            if ((rc = dmalloc(&b->P32, (size_t)b->total)) || (rc = dmalloc(&b->Q32, (size_t)b->total)) ||
+                (rc = dmalloc(&b->d_mats_lo, b->nmat)))
+                return rc;
+        }
+        if (b->lo_vt != lo) {
+            if ((rc = fill_table(b, b->d_mats_lo, b->P32, b->Q32, lo, 1))) return rc;
+            b->lo_vt = lo;
+        }
+    }
+    const int key[3] = {inner, replace_every, restart};
+    if (!b->sexec || std::memcmp(key, b->sexec_key, sizeof(key)) != 0) {
+        if (b->sexec) {
+            cudaGraphExecDestroy(b->sexec);
+            b->sexec = nullptr;
+        }
+        CK_CUDA(cudaStreamSynchronize(s), "synchronise");
+        rc = bcg_capture(b, &b->sexec,
+                         [&](cudaStream_t cs) { return bsolve_enqueue_cycle(b, cs, mixed, replace_every, restart); });
+        if (rc) return rc;
+        std::memcpy(b->sexec_key, key, sizeof(key));
+    }
+    CK_CUDA(cudaMemcpyAsync(b->d_ptrs_in, B, b->nmat * sizeof(double*), cudaMemcpyHostToDevice, s), "B pointers");
+    CK_CUDA(cudaMemcpyAsync(b->d_ptrs_out, Xout, b->nmat * sizeof(double*), cudaMemcpyHostToDevice, s), "X pointers");
+    const dim3 cg_grid(64, std::min<int32_t>(b->nmat, 65535));
+    bcg_gather<<<cg_grid, 256, 0, s>>>(b->d_ptrs_in, b->d_moff, b->d_mlen, b->nmat, b->B);
+    bcg_init<<<b->nchunks, VT_THREADS, 0, s>>>(b->d_chunks, b->d_mats_pq, b->B, b->X, b->R, b->P,
+                                               mixed ? b->P32 : nullptr, b->partials);
+    bcg_fin(b, s, 0, rtol);
+    CK_CUDA(cudaGetLastError(), "batched CG init");
+    const int32_t max_cycles = (maxit + replace_every - 1) / replace_every;
+    int32_t cycles = 0;
+    for (; cycles < max_cycles;) {
+        CK_CUDA(cudaGraphLaunch(b->sexec, s), "graph launch");
+        ++cycles;
+        CK_CUDA(cudaMemcpyAsync(b->h_active, b->d_active, sizeof(int32_t), cudaMemcpyDeviceToHost, s), "read counter");
+        CK_CUDA(cudaStreamSynchronize(s), "synchronise");
+        if (*b->h_active == 0) break;
+    }
+    bcg_scatter<<<cg_grid, 256, 0, s>>>(b->X, b->d_moff, b->d_mlen, b->nmat, b->d_ptrs_out);
+    CK_CUDA(cudaGetLastError(), "batched CG finish");
+    std::vector<SysState> hs(b->nsys);
+    CK_CUDA(cudaMemcpyAsync(hs.data(), b->st, b->nsys * sizeof(SysState), cudaMemcpyDeviceToHost, s), "read state");
+    CK_CUDA(cudaStreamSynchronize(s), "synchronise");
+    bool all = true;
+    for (int32_t q = 0; q < b->nsys; ++q) {
+        if (relres) relres[q] = hs[q].bb > 0.0 ? std::sqrt(hs[q].rr_true / hs[q].bb) : 0.0;
+        if (iters_done) iters_done[q] = hs[q].iters;
+        all = all && hs[q].done == 1;
+    }
+    if (cycles_out) *cycles_out = cycles;
+    if (!all) return fail(CSRK_ERR_NOT_CONVERGED, "some systems did not reach rtol (or broke down)");
     return CSRK_OK;
 }
 

@@ -63,6 +63,7 @@ _PROTOS = {
     "csrk_batch_cg": [_vp, _vp, _vp, _i32, _d, _vp, _vp, _vp],
     "csrk_batch_info": [_vp, _pi32, _pi32, _pi32, _pi64],
     "csrk_batch_plan": [_vp, _pi32, _pi32, _pi32],
+    "csrk_batch_cg_solve": [_vp, _vp, _vp, _d, _i32, ctypes.c_int, _i32, ctypes.c_int, _vp, _vp, _pi32, _vp],
     "csrk_batch_device_status": [_vp, _pi32],
     "csrk_batch_destroy": [_vp],
     "csrk_spmv_static_scratch": [_i32, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _d, _vp, _d, _vp, _vp],
@@ -289,6 +290,22 @@ def batch_cg(b, Bs, Xs, iters, rtol=1e-10, stream=None):
                                rel.ctypes.data_as(_vp), its.ctypes.data_as(_vp), _stream(stream, *Bs)),
            "csrk_batch_cg")
     return rel, its
+
+
+def batch_cg_solve(b, Bs, Xs, rtol=1e-10, maxit=2000, inner="f64", replace_every=20, restart=0,
+                   stream=None, check=True):
+    """CG to rtol for every system of the batch; returns (status, relres, iterations, cycles)
+    with one relres / iteration count per system (matrix-major, then column)."""
+    nsys = batch_info(b)["nsys"]
+    rel = np.empty(nsys, np.float64)
+    its = np.empty(nsys, np.int32)
+    cyc = ctypes.c_int32()
+    rc = lib().csrk_batch_cg_solve(b, _ptr_array(Bs), _ptr_array(Xs), float(rtol), int(maxit), DTYPES[inner],
+                                   int(replace_every), int(restart), rel.ctypes.data_as(_vp),
+                                   its.ctypes.data_as(_vp), ctypes.byref(cyc), _stream(stream, *Bs))
+    if check and rc not in (0, 8):
+        _check(rc, "csrk_batch_cg_solve")
+    return rc, rel, its, cyc.value
 
 
 def batch_destroy(b):

@@ -3,6 +3,7 @@ import numpy as np
 import pytest
 
 import synth
+from oracle import cg as ocg
 from oracle import precision
 from oracle import spmv as ospmv
 
@@ -170,3 +171,94 @@ def test_batch_rejects_natural_numbering():
     assert ei.value.status == "ERR_UNSUPPORTED"
     csrk.batch_destroy(b)
     csrk.destroy(h)
+
+
+SOLVE_SPECS = [(synth.stencil_3d(14, 13, 12, 27, "random_dd", 31), "f64", 4, (32, 4)),
+               (synth.stencil_3d(20, 20, 9, 7, "random_dd", 32), "f32", 1, (32, 8)),
+               (synth.fem_like(8, 33), "f32", 2, (32, 2)),
+               (synth.stencil_3d(6, 6, 6, 27, "random_dd", 34), "f64", 16, (16, 4)),
+               (synth.stencil_2d_5pt(17, 13), "bf16", 8, (32, 1))]
+
+
+def solve_setup(specs):
+    hs, forms = [], []
+    for a, dtype, k, sizes in specs:
+        h = csrk.create(a.n, a.rowptr, a.colidx, a.vals, dtype)
+        csrk.reorder(h)
+        csrk.set_sizes(h, *sizes)
+        e = csrk.export(h)
+        forms.append((e["rowptr"], e["colidx"], e["vals"]))   # the FP64 operator
+        hs.append(h)
+    b = csrk.batch_create(hs, [k for _, _, k, _ in specs])
+    Bs = [torch.tensor(synth.uniform_block(a.n, k, 600 + i), device=DEV) for i, (a, _, k, _) in enumerate(specs)]
+    return hs, forms, b, Bs
+
+
+@pytest.mark.parametrize("inner,restart", [("f64", 0), ("f32", 0), ("bf16", 1)])
+def test_batch_cg_solve_reaches_rtol_on_the_fp64_operator(inner, restart):
+    hs, forms, b, Bs = solve_setup(SOLVE_SPECS)
+    Xs = [torch.full_like(x, np.nan) for x in Bs]
+    rc, rel, its, cycles = csrk.batch_cg_solve(b, Bs, Xs, rtol=1e-10, maxit=3000, inner=inner, restart=restart)
+    assert rc == 0 and cycles >= 1
+    assert np.all(rel <= 1e-10), rel
+    q = 0
+    for i, ((a, _, k, _), (rp, ci, v)) in enumerate(zip(SOLVE_SPECS, forms)):
+        X, B = Xs[i].cpu().numpy(), Bs[i].cpu().numpy()
+        for c in range(k):
+            true = np.linalg.norm(B[:, c] - ospmv.csr_spmv(a.n, rp, ci, v, X[:, c])) / np.linalg.norm(B[:, c])
+            assert true <= 1.05e-10 and abs(true - rel[q]) <= 1e-13 + 1e-3 * true, (i, c, true, rel[q])
+            if inner == "f64":          # same recurrences, same stopping rule: same count up to rounding
+                _, it_ref, _ = ocg.cg_fp64(a.n, rp, ci, v, B[:, c], rtol=1e-10)
+                assert abs(int(its[q]) - it_ref) <= 3, (i, c, its[q], it_ref)
+            else:                       # the oracle's mixed CG sums the rounded products in FP64
+                _, it_ref, res_ref = ocg.cg_mixed(a.n, rp, ci, v, B[:, c], lo=inner, rtol=1e-10,
+                                                  replace_every=20, restart=bool(restart))
+                assert res_ref <= 1e-10 and abs(int(its[q]) - it_ref) <= max(8, 0.25 * it_ref), (i, c, its[q], it_ref)
+            q += 1
+    # a second solve replays the cycle graph and reproduces the result exactly
+    Xs2 = [torch.zeros_like(x) for x in Bs]
+    rc2, rel2, its2, cycles2 = csrk.batch_cg_solve(b, Bs, Xs2, rtol=1e-10, maxit=3000, inner=inner, restart=restart)
+    assert rc2 == 0 and cycles2 == cycles and np.array_equal(its, its2) and np.array_equal(rel, rel2)
+    assert all(torch.equal(x, y) for x, y in zip(Xs, Xs2))
+    assert csrk.batch_device_status(b) == 0
+    csrk.batch_destroy(b)
+    for h in hs:
+        csrk.destroy(h)
+
+
+def test_batch_cg_solve_matches_oracle_mixed_iterations():
+    """One system per matrix: the mixed solve against the oracle's mixed CG (which sums the
+    low-precision products in FP64, so counts agree only roughly)."""
+    specs = [(synth.stencil_3d(16, 16, 16, 27, "random_dd", 41), "f64", 1, (32, 4)),
+             (synth.fem_like(10, 42), "f64", 1, (32, 2))]
+    hs, forms, b, Bs = solve_setup(specs)
+    Xs = [torch.zeros_like(x) for x in Bs]
+    rc, rel, its, _ = csrk.batch_cg_solve(b, Bs, Xs, rtol=1e-10, maxit=3000, inner="f32", restart=1)
+    assert rc == 0
+    for i, ((a, _, k, _), (rp, ci, v)) in enumerate(zip(specs, forms)):
+        B = Bs[i].cpu().numpy()[:, 0]
+        _, it_ref, res_ref = ocg.cg_mixed(a.n, rp, ci, v, B, lo="f32", rtol=1e-10, replace_every=20, restart=True)
+        assert res_ref <= 1e-10 and abs(int(its[i]) - it_ref) <= max(5, 0.15 * it_ref), (i, its[i], it_ref)
+    csrk.batch_destroy(b)
+    for h in hs:
+        csrk.destroy(h)
+
+
+def test_batch_cg_solve_iteration_limit_and_fallback(monkeypatch):
+    hs, forms, b, Bs = solve_setup(SOLVE_SPECS[:2])
+    Xs = [torch.zeros_like(x) for x in Bs]
+    rc, rel, its, cycles = csrk.batch_cg_solve(b, Bs, Xs, rtol=1e-10, maxit=20, inner="f64")
+    assert rc == 8 and cycles == 1 and np.all(its <= 20) and np.any(rel > 1e-10)   # CSRK_ERR_NOT_CONVERGED
+    csrk.batch_destroy(b)
+    # the direct-load kernel: FP64 solves run, mixed ones are refused
+    monkeypatch.setenv("CSRK_BATCH_ITEM_BYTES", str(1 << 30))
+    b = csrk.batch_create(hs, [k for _, _, k, _ in SOLVE_SPECS[:2]])
+    assert csrk.batch_plan(b)["stages"] == 0
+    rc, rel, _, _ = csrk.batch_cg_solve(b, Bs, Xs, rtol=1e-10, maxit=3000, inner="f64")
+    assert rc == 0 and np.all(rel <= 1e-10)
+    with pytest.raises(csrk.CsrkError) as ei:
+        csrk.batch_cg_solve(b, Bs, Xs, inner="f32")
+    assert ei.value.status == "ERR_UNSUPPORTED"
+    csrk.batch_destroy(b)
+    for h in hs:
+        csrk.destroy(h)

@@ -260,6 +260,40 @@ def test_vec_permuted_and_permute_entry_point():
     csrk.destroy(h)
 
 
+@pytest.mark.parametrize("dims", [(6, 6, 6), (5, 5, 1), (7, 7, 2), (3, 3, 3), (3, 1, 1)])   # n % 4 = 0, 1, 2, 3; n < 4
+def test_permute_paths_bit_exact(dims):
+    """Gather and scatter through the quad kernel (aligned unit stride), the element-wise
+    kernel (a view 8 bytes off a 16-byte boundary) and the k > 1 kernel."""
+    nx, ny, nz = dims
+    side = nx * ny * nz
+    a = synth.stencil_3d(nx, ny, nz, 7, "random_dd", side, labels=synth.vectors.permutation(side, side))
+    h = make(a)
+    perm = csrk.export(h)["perm"]
+    n = a.n
+    x = synth.uniform_vector(n + 1, 40 + side)
+    base = torch.tensor(x, device=DEV)
+    for xt in (base[:n], base[1:]):                    # 16-byte aligned, then 8-byte aligned
+        xv = xt.cpu().numpy()
+        outb = torch.full((n + 1,), np.nan, dtype=torch.float64, device=DEV)
+        for out in (outb[:n], outb[1:]):
+            csrk.permute(h, 0, 1, xt, 1, out, 1)
+            torch.cuda.synchronize()
+            assert np.array_equal(out.cpu().numpy(), xv[perm])
+            csrk.permute(h, 1, 1, xt, 1, out, 1)
+            torch.cuda.synchronize()
+            back = np.empty(n)
+            back[perm] = xv
+            assert np.array_equal(out.cpu().numpy(), back)
+    X = synth.uniform_block(n, 5, 50 + side)
+    Xt = torch.tensor(X, device=DEV)
+    Yt = torch.full((n, 5), np.nan, dtype=torch.float64, device=DEV)
+    csrk.permute(h, 0, 3, Xt, 5, Yt, 5)               # k = 3 of ld 5
+    torch.cuda.synchronize()
+    got = Yt.cpu().numpy()
+    assert np.array_equal(got[:, :3], X[perm, :3]) and np.isnan(got[:, 3:]).all()
+    csrk.destroy(h)
+
+
 def test_x_permuted_flag_scatters_y():
     a = small_27pt(15)
     x = synth.uniform_vector(a.n, 28)
