@@ -464,6 +464,25 @@ def run_batch(args, dev, stream, peak):
            "spmm_bound": "fp64", "fp64_peak_gflops": FP64_NOMINAL_GFLOPS,
            "spmm_frac_of_fp64": round(flops / (ms * 1e-3) / 1e9 / FP64_NOMINAL_GFLOPS, 3),
            "plan": csrk.batch_plan(b)}
+    # the same product in FP32 arithmetic (values rounded to FP32, FP32 vectors and
+    # accumulation): memory-bound, the inner product of the mixed-precision solve
+    X32 = [x.float() for x in Xs]
+    Y32 = [torch.empty_like(x) for x in X32]
+    f32 = csrk.VEC_PERMUTED | csrk.X_F32 | csrk.ACC_F32
+    for _ in range(3):
+        csrk.batch_spmm(b, 1.0, X32, 0.0, Y32, flags=f32)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        csrk.batch_spmm(b, 1.0, X32, 0.0, Y32, flags=f32)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms32 = e0.elapsed_time(e1) / reps
+    vbytes32 = sum(({"f64": 4, "f32": 4, "bf16": 2}[sp["dtype"]] + 4) * nnz + 4 * (n + 1) + 8 * n * sp["k"]
+                   for (n, nnz, sp) in mats)
+    out["spmm_f32"] = {"ms": round(ms32, 4), "gflops": round(flops / (ms32 * 1e-3) / 1e9, 1),
+                       "gbs": round(vbytes32 / (ms32 * 1e-3) / 1e9, 1), "bound": "hbm",
+                       "frac_of_peak": round(vbytes32 / (ms32 * 1e-3) / 1e9 / peak, 3)}
     if args.no_cg:
         csrk.batch_destroy(b)
         for h in hs:
@@ -490,7 +509,9 @@ def run_batch(args, dev, stream, peak):
         torch.cuda.synchronize()
         s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         s0.record(stream)
+        torch.cuda.nvtx.range_push(f"solve_{inner}")   # lets a profiler keep one solve's launches
         rc, rel, its, cycles = csrk.batch_cg_solve(b, Bs, Xs, rtol=1e-10, maxit=2000, inner=inner, restart=rst)
+        torch.cuda.nvtx.range_pop()
         s1.record(stream)
         torch.cuda.synchronize()
         solve[inner] = {"ms": round(s0.elapsed_time(s1), 3), "converged_systems": int(np.sum(rel <= 1e-10)),

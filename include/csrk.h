@@ -219,8 +219,14 @@ int csrk_batch_create(const csrk_handle* hs, int32_t count, const int32_t* k,
  * in each block a producer warp stages the tiles' items into shared memory with bulk
  * copies while the other warps compute).  Every wait inside the kernel is bounded (2 s);
  * one that gives up sets a bit of the batch's status word (csrk_batch_device_status).
- *   X, Y    host arrays of count DEVICE pointers (X[i], Y[i]: n_i x k_i FP64 blocks)
- *   flags   must be CSRK_VEC_PERMUTED
+ *   X, Y    host arrays of count DEVICE pointers (X[i], Y[i]: n_i x k_i blocks, FP64, or
+ *           FP32 with CSRK_X_F32)
+ *   flags   CSRK_VEC_PERMUTED: FP64 vectors, FP64 accumulation, each matrix's stored values;
+ *           CSRK_VEC_PERMUTED | CSRK_X_F32 | CSRK_ACC_F32: FP32 vectors and FP32
+ *           accumulation, FP32 values (FP64-stored matrices use their values rounded to
+ *           FP32; BF16 stays BF16) -- needs the staged kernel (else CSRK_ERR_UNSUPPORTED)
+ * Blocks on 16-byte boundaries with a power-of-two k gather k/VW-lane groups of VW columns
+ * with one vector load per nonzero (VW = 2 for FP64, 4 for FP32 with k >= 4).
  * A call with the same pointers as the previous one reuses the device-side table (one
  * launch, no copy); new pointers cost one small host-to-device copy first. */
 int csrk_batch_spmm(csrk_batch_handle b, double alpha, const void* const* X, double beta,

@@ -46,6 +46,8 @@ struct BatchMat {
     void* Y;
     int32_t n, k, vt;
     int32_t xt;      // 1: FP32 vectors and FP32 accumulation (FP32 / BF16 values only)
+    int32_t vec;     // X and Y blocks 16-byte aligned: power-of-two k use vector loads
+    int32_t pad;
 };
 
 struct BatchTile {
@@ -157,8 +159,13 @@ __host__ __device__ inline void slice16_rt(int64_t first, int64_t last, int esz,
 
 __host__ __device__ inline int val_bytes_of(int vt) { return vt == csrk::VAL_F64 ? 8 : vt == csrk::VAL_F32 ? 4 : 2; }
 
-// Rows one warp pass covers for k right-hand sides (the lane mapping of sr_rows).
-__device__ __forceinline__ int rows_per_pass(int k) {
+// Rows one warp pass covers for k right-hand sides: the lane mapping of item_rows, or of
+// item_rows_vec (VW columns per lane) for aligned power-of-two k.
+__device__ __forceinline__ int rows_per_pass(int k, bool vec, int xbytes) {
+    if (vec && k >= 2 && k <= 32 && (k & (k - 1)) == 0) {
+        const int vw = xbytes == 4 ? (k == 2 ? 2 : 4) : 2;
+        return 32 / (k / vw);
+    }
     return k == 1 ? 32 : k == 2 ? 16 : k <= 4 ? 8 : k <= 8 ? 4 : k <= 16 ? 2 : 1;
 }
 
@@ -182,6 +189,74 @@ __device__ __noinline__ void item_rows(const XT* X, XT* Y, int k, int r0, int r1
     }
 }
 
+template <typename XT, int VW> struct VecT;
+template <> struct VecT<float, 2> { using T = float2; };
+template <> struct VecT<float, 4> { using T = float4; };
+template <> struct VecT<double, 2> { using T = double2; };
+
+// As item_rows for k = G * VW right-hand sides with 16-byte aligned X / Y blocks: each lane
+// owns VW consecutive columns and gathers them with one vector load per nonzero (a 16-byte
+// request instead of VW separate ones), chunks of 4 nonzeros in flight per lane.
+template <typename VT, typename XT, typename AT, int G, int VW>
+__device__ __noinline__ void item_rows_vec(const XT* X, XT* Y, int k, int r0, int r1, int p0, int first,
+                                           const int32_t* rp, const int32_t* col, const unsigned char* vb,
+                                           double alpha, double beta, int epi, int lane) {
+    using namespace csrk::dev;
+    using V = typename VecT<XT, VW>::T;
+    constexpr int VPER = 16 / (int)sizeof(VT);
+    const VT* val = reinterpret_cast<const VT*>(vb) - (p0 & ~(VPER - 1));
+    constexpr int RPP = 32 / G;
+    constexpr int U = 4;
+    const int c0 = (lane % G) * VW;
+    const int ng = (r1 - r0 + RPP - 1) / RPP;
+    for (int g = first; g < ng; g += TW) {
+        const int r = r0 + g * RPP + lane / G;
+        if (r >= r1) continue;
+        AT acc[VW];
+#pragma unroll
+        for (int j = 0; j < VW; ++j) acc[j] = 0;
+        const int pe = rp[r + 1];
+        int p = rp[r];
+        for (; p + U <= pe; p += U) {
+            V xv[U];
+#pragma unroll
+            for (int t = 0; t < U; ++t) xv[t] = __ldg(reinterpret_cast<const V*>(X + (int64_t)col[p + t] * k + c0));
+#pragma unroll
+            for (int t = 0; t < U; ++t) {
+                const VT v = val[p + t];
+                const XT* e = reinterpret_cast<const XT*>(&xv[t]);
+#pragma unroll
+                for (int j = 0; j < VW; ++j) acc[j] = Acc<AT>::fma(v, e[j], acc[j]);
+            }
+        }
+        if (p < pe) {   // the last 1..3 nonzeros
+            V xv[U];
+#pragma unroll
+            for (int t = 0; t < U; ++t)
+                if (p + t < pe) xv[t] = __ldg(reinterpret_cast<const V*>(X + (int64_t)col[p + t] * k + c0));
+#pragma unroll
+            for (int t = 0; t < U; ++t)
+                if (p + t < pe) {
+                    const VT v = val[p + t];
+                    const XT* e = reinterpret_cast<const XT*>(&xv[t]);
+#pragma unroll
+                    for (int j = 0; j < VW; ++j) acc[j] = Acc<AT>::fma(v, e[j], acc[j]);
+                }
+        }
+        XT* yr = Y + (int64_t)r * k + c0;
+        if (epi == 0) {
+            V out;
+            XT* o = reinterpret_cast<XT*>(&out);
+#pragma unroll
+            for (int j = 0; j < VW; ++j) o[j] = (XT)acc[j];
+            *reinterpret_cast<V*>(yr) = out;
+        } else {
+#pragma unroll
+            for (int j = 0; j < VW; ++j) store_y<XT, AT>(yr, j, acc[j], alpha, beta, epi);
+        }
+    }
+}
+
 template <typename VT, typename XT, typename AT>
 __device__ __forceinline__ void item_dispatch(const BatchMat* m, int r0, int r1, int p0, int first,
                                               const int32_t* rp, const int32_t* col, const unsigned char* vb,
@@ -189,6 +264,25 @@ __device__ __forceinline__ void item_dispatch(const BatchMat* m, int r0, int r1,
     const int k = m->k;
     const XT* X = static_cast<const XT*>(m->X);
     XT* Y = static_cast<XT*>(m->Y);
+    if (m->vec && k >= 2 && k <= 32 && (k & (k - 1)) == 0) {
+#define CSRK_ITEMV(G, VW) \
+    item_rows_vec<VT, XT, AT, G, VW>(X, Y, k, r0, r1, p0, first, rp, col, vb, alpha, beta, epi, lane)
+        if constexpr (sizeof(XT) == 4) {   // float2 for k = 2, float4 otherwise
+            if (k == 2) CSRK_ITEMV(1, 2);
+            else if (k == 4) CSRK_ITEMV(1, 4);
+            else if (k == 8) CSRK_ITEMV(2, 4);
+            else if (k == 16) CSRK_ITEMV(4, 4);
+            else CSRK_ITEMV(8, 4);
+        } else {                           // double2
+            if (k == 2) CSRK_ITEMV(1, 2);
+            else if (k == 4) CSRK_ITEMV(2, 2);
+            else if (k == 8) CSRK_ITEMV(4, 2);
+            else if (k == 16) CSRK_ITEMV(8, 2);
+            else CSRK_ITEMV(16, 2);
+        }
+#undef CSRK_ITEMV
+        return;
+    }
 #define CSRK_ITEM(G, CPL) item_rows<VT, XT, AT, G, CPL>(X, Y, k, r0, r1, p0, first, rp, col, vb, alpha, beta, epi, lane)
     if (k == 1) CSRK_ITEM(1, 1);
     else if (k == 2) CSRK_ITEM(2, 1);
@@ -302,7 +396,7 @@ __global__ void __launch_bounds__((TW + 1) * 32, 2)
             const int32_t* rp = reinterpret_cast<const int32_t*>(st) - (h.r0 & ~3);
             const int32_t* col = reinterpret_cast<const int32_t*>(st + h.off_col) - (h.p0 & ~3);
             const unsigned char* vb = st + h.off_val;
-            const int rpp = rows_per_pass(m->k);
+            const int rpp = rows_per_pass(m->k, m->vec != 0, m->xt ? 4 : 8);
             const int ng = (h.r1 - h.r0 + rpp - 1) / rpp;
             const int first = (warp - seq + TW) % TW;
             seq = (seq + ng) % TW;
@@ -383,6 +477,11 @@ __global__ void __launch_bounds__(VT_THREADS) bcg_init(const Chunk* __restrict__
 __device__ __forceinline__ double as_f64(double v) { return v; }
 __device__ __forceinline__ double as_f64(float v) { return (double)v; }
 
+// The hot vector kernels walk a chunk CHUNK_ILP elements per thread per trip (e, e + 256,
+// ...), issuing all of a trip's loads before any arithmetic, so each thread keeps several
+// independent requests in flight.  Thread t still sees only column t % k.
+constexpr int CHUNK_ILP = 4;
+
 // partial A.B per system; B is FP64 or the FP32 product of a mixed solve
 template <typename TB>
 __global__ void __launch_bounds__(VT_THREADS) bcg_dot(const Chunk* __restrict__ chunks, const BatchMat* mats,
@@ -392,7 +491,17 @@ __global__ void __launch_bounds__(VT_THREADS) bcg_dot(const Chunk* __restrict__ 
     const int k = mats[ch.mat].k;
     const int64_t e0 = ch.off, e1 = ch.off + (int64_t)(ch.row1 - ch.row0) * k;
     double v = 0.0;
-    for (int64_t e = e0 + threadIdx.x; e < e1; e += VT_THREADS) v += A[e] * as_f64(Bv[e]);
+    for (int64_t e = e0 + threadIdx.x; e < e1; e += CHUNK_ILP * VT_THREADS) {
+        double a[CHUNK_ILP], b[CHUNK_ILP];
+#pragma unroll
+        for (int u = 0; u < CHUNK_ILP; ++u) {
+            const int64_t q = e + u * VT_THREADS;
+            a[u] = q < e1 ? A[q] : 0.0;
+            b[u] = q < e1 ? as_f64(Bv[q]) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < CHUNK_ILP; ++u) v += a[u] * b[u];
+    }
     chunk_partial(v, k, partials + (int64_t)blockIdx.x * 32);
 }
 
@@ -400,18 +509,36 @@ __global__ void __launch_bounds__(VT_THREADS) bcg_dot(const Chunk* __restrict__ 
 template <typename TQ>
 __global__ void __launch_bounds__(VT_THREADS) bcg_update_xr(const Chunk* __restrict__ chunks, const BatchMat* mats,
                                                             const int32_t* sys_off, const SysState* st,
-                                                            double* X, double* R, const double* __restrict__ P,
+                                                            double* __restrict__ X, double* __restrict__ R,
+                                                            const double* __restrict__ P,
                                                             const TQ* __restrict__ Q, double* partials) {
     const Chunk ch = chunks[blockIdx.x];
     const int k = mats[ch.mat].k;
     const int64_t e0 = ch.off, e1 = ch.off + (int64_t)(ch.row1 - ch.row0) * k;
     const double alpha = st[sys_of(sys_off, ch.mat, threadIdx.x % k)].alpha;
     double v = 0.0;
-    for (int64_t e = e0 + threadIdx.x; e < e1; e += VT_THREADS) {
-        X[e] += alpha * P[e];
-        const double r = R[e] - alpha * as_f64(Q[e]);
-        R[e] = r;
-        v += r * r;
+    for (int64_t e = e0 + threadIdx.x; e < e1; e += CHUNK_ILP * VT_THREADS) {
+        double x[CHUNK_ILP], r[CHUNK_ILP], p[CHUNK_ILP], q[CHUNK_ILP];
+#pragma unroll
+        for (int u = 0; u < CHUNK_ILP; ++u) {
+            const int64_t i = e + u * VT_THREADS;
+            if (i < e1) {
+                x[u] = X[i];
+                r[u] = R[i];
+                p[u] = P[i];
+                q[u] = as_f64(Q[i]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < CHUNK_ILP; ++u) {
+            const int64_t i = e + u * VT_THREADS;
+            if (i < e1) {
+                X[i] = x[u] + alpha * p[u];
+                const double rn = r[u] - alpha * q[u];
+                R[i] = rn;
+                v += rn * rn;
+            }
+        }
     }
     chunk_partial(v, k, partials + (int64_t)blockIdx.x * 32);
 }
@@ -419,15 +546,31 @@ __global__ void __launch_bounds__(VT_THREADS) bcg_update_xr(const Chunk* __restr
 // P = R + beta P (and P32 = P rounded to FP32 when given)
 __global__ void __launch_bounds__(VT_THREADS) bcg_update_p(const Chunk* __restrict__ chunks, const BatchMat* mats,
                                                            const int32_t* sys_off, const SysState* st,
-                                                           const double* __restrict__ R, double* P, float* P32) {
+                                                           const double* __restrict__ R, double* __restrict__ P,
+                                                           float* __restrict__ P32) {
     const Chunk ch = chunks[blockIdx.x];
     const int k = mats[ch.mat].k;
     const int64_t e0 = ch.off, e1 = ch.off + (int64_t)(ch.row1 - ch.row0) * k;
     const double beta = st[sys_of(sys_off, ch.mat, threadIdx.x % k)].beta;
-    for (int64_t e = e0 + threadIdx.x; e < e1; e += VT_THREADS) {
-        const double p = R[e] + beta * P[e];
-        P[e] = p;
-        if (P32) P32[e] = (float)p;
+    for (int64_t e = e0 + threadIdx.x; e < e1; e += CHUNK_ILP * VT_THREADS) {
+        double r[CHUNK_ILP], p[CHUNK_ILP];
+#pragma unroll
+        for (int u = 0; u < CHUNK_ILP; ++u) {
+            const int64_t i = e + u * VT_THREADS;
+            if (i < e1) {
+                r[u] = R[i];
+                p[u] = P[i];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < CHUNK_ILP; ++u) {
+            const int64_t i = e + u * VT_THREADS;
+            if (i < e1) {
+                const double pn = r[u] + beta * p[u];
+                P[i] = pn;
+                if (P32) P32[i] = (float)pn;
+            }
+        }
     }
 }
 
@@ -581,9 +724,12 @@ struct csrk_batch {
     int32_t *d_mat_chunk0 = nullptr, *d_mat_chunk1 = nullptr;
     int64_t *d_moff = nullptr, *d_mlen = nullptr;
     std::vector<BatchMat> h_mats;
-    std::vector<const void*> bound_x;
-    std::vector<void*> bound_y;
+    std::vector<int64_t> h_moff;     // element offset of each matrix's block in the concatenated vectors
+    std::vector<const void*> bound_x, bound_x32;
+    std::vector<void*> bound_y, bound_y32;
     BatchMat* h_pinned_mats = nullptr;
+    BatchMat* d_mats_user32 = nullptr;   // csrk_batch_spmm with FP32 vectors
+    BatchMat* h_pinned_mats32 = nullptr;
     // CG buffers
     double *B = nullptr, *X = nullptr, *R = nullptr, *P = nullptr, *Q = nullptr, *partials = nullptr;
     // csrk_batch_cg_solve: FP32 copies of P and of the inner product, operator tables
@@ -629,8 +775,9 @@ void batch_free(csrk_batch* b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->sexec) cudaGraphExecDestroy(b->sexec);
     for (void* p : {(void*)b->P32, (void*)b->Q32, (void*)b->d_mats_pq64, (void*)b->d_mats_lo,
-                    (void*)b->d_mats_t64, (void*)b->d_active})
+                    (void*)b->d_mats_t64, (void*)b->d_active, (void*)b->d_mats_user32})
         cudaFree(p);
+    if (b->h_pinned_mats32) cudaFreeHost(b->h_pinned_mats32);
     if (b->h_active) cudaFreeHost(b->h_active);
     for (void* p : {(void*)b->d_mats_user, (void*)b->d_mats_pq, (void*)b->d_mats_xr, (void*)b->d_tiles,
                     (void*)b->d_items, (void*)b->d_itiles, (void*)b->d_status, (void*)b->d_counters, (void*)b->d_chunks, (void*)b->d_sys_mat, (void*)b->d_sys_col,
@@ -667,7 +814,6 @@ int launch_batch_spmm(csrk_batch* b, const BatchMat* table, double alpha, double
 int fill_table(csrk_batch* b, BatchMat* table, const void* xbase, void* ybase, int vt = -1, int xt = 0) {
     std::vector<BatchMat> t = b->h_mats;
     const size_t esz = xt ? sizeof(float) : sizeof(double);
-    int64_t off = 0;
     for (int32_t i = 0; i < b->nmat; ++i) {
         if (vt >= 0) {
             int rc = ensure_vals(b->hs[i], vt);
@@ -676,9 +822,9 @@ int fill_table(csrk_batch* b, BatchMat* table, const void* xbase, void* ybase, i
             t[i].vt = vt;
         }
         t[i].xt = xt;
-        t[i].X = static_cast<const unsigned char*>(xbase) + off * esz;
-        t[i].Y = static_cast<unsigned char*>(ybase) + off * esz;
-        off += (int64_t)t[i].n * t[i].k;
+        t[i].vec = 1;   // cudaMalloc'd base, block offsets multiples of 4 elements
+        t[i].X = static_cast<const unsigned char*>(xbase) + b->h_moff[i] * esz;
+        t[i].Y = static_cast<unsigned char*>(ybase) + b->h_moff[i] * esz;
     }
     CK_CUDA(cudaMemcpy(table, t.data(), t.size() * sizeof(BatchMat), cudaMemcpyHostToDevice), "batch table");
     return CSRK_OK;
@@ -785,7 +931,7 @@ int csrk_batch_create(const csrk_handle* hs, int32_t count, const int32_t* k, cs
             mc1[i] = (int32_t)chunks.size();
             moff[i] = off;
             mlen[i] = (int64_t)m.n * k[i];
-            off += mlen[i];
+            off += (mlen[i] + 3) & ~int64_t(3);   // every block 16-byte aligned (FP32) / 32-byte (FP64)
         }
         if (!rc) {
             // Matrices in order of decreasing total work; within a matrix, tiles in SSR
@@ -851,6 +997,7 @@ int csrk_batch_create(const csrk_handle* hs, int32_t count, const int32_t* k, cs
             if (!rc) rc = upload(&b->d_sys_off, sys_off);
             if (!rc) rc = upload(&b->d_mat_chunk0, mc0);
             if (!rc) rc = upload(&b->d_mat_chunk1, mc1);
+            b->h_moff = moff;
             if (!rc) rc = upload(&b->d_moff, moff);
             if (!rc) rc = upload(&b->d_mlen, mlen);
             if (!rc) rc = dmalloc(&b->d_mats_user, count);
@@ -877,28 +1024,51 @@ int csrk_batch_create(const csrk_handle* hs, int32_t count, const int32_t* k, cs
 int csrk_batch_spmm(csrk_batch_handle b, double alpha, const void* const* X, double beta,
                     void* const* Y, unsigned flags, void* stream) {
     if (!b || !X || !Y) return fail(CSRK_ERR_ARG, "NULL argument");
-    if (!(flags & CSRK_VEC_PERMUTED) || (flags & ~CSRK_VEC_PERMUTED))
-        return fail(CSRK_ERR_UNSUPPORTED, "batched calls take FP64 vectors in the reordered numbering "
-                                          "(flags = CSRK_VEC_PERMUTED)");
+    const unsigned f32 = CSRK_VEC_PERMUTED | CSRK_X_F32 | CSRK_ACC_F32;
+    if (flags != CSRK_VEC_PERMUTED && flags != f32)
+        return fail(CSRK_ERR_UNSUPPORTED, "batched SpMM takes vectors in the reordered numbering: flags = "
+                                          "CSRK_VEC_PERMUTED (FP64), or with CSRK_X_F32 | CSRK_ACC_F32 (FP32)");
+    const int xt = flags == f32 ? 1 : 0;
+    if (xt && b->stages < 2)
+        return fail(CSRK_ERR_UNSUPPORTED, "FP32 batched SpMM needs the staged kernel "
+                                          "(super-rows too large for two shared-memory stages)");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int rc;
+    if (xt && !b->d_mats_user32) {
+        if ((rc = dmalloc(&b->d_mats_user32, b->nmat))) return rc;
+        if (cudaMallocHost(&b->h_pinned_mats32, b->nmat * sizeof(BatchMat)) != cudaSuccess)
+            return fail(CSRK_ERR_ALLOC, "batch pinned table");
+        for (int32_t i = 0; i < b->nmat; ++i)   // FP64-stored values are used rounded to FP32
+            if (b->hs[i]->dtype == CSRK_F64 && (rc = ensure_vals(b->hs[i], csrk::VAL_F32))) return rc;
+    }
+    BatchMat* table = xt ? b->d_mats_user32 : b->d_mats_user;
+    BatchMat* pinned = xt ? b->h_pinned_mats32 : b->h_pinned_mats;
+    std::vector<const void*>& bx = xt ? b->bound_x32 : b->bound_x;
+    std::vector<void*>& by = xt ? b->bound_y32 : b->bound_y;
     // re-bind the vectors only when they changed (the table lives on the device)
-    bool same = b->bound_x.size() == (size_t)b->nmat;
-    for (int32_t i = 0; same && i < b->nmat; ++i) same = b->bound_x[i] == X[i] && b->bound_y[i] == Y[i];
+    bool same = bx.size() == (size_t)b->nmat;
+    for (int32_t i = 0; same && i < b->nmat; ++i) same = bx[i] == X[i] && by[i] == Y[i];
     if (!same) {
         // the pinned staging table may still feed an earlier copy: wait for it first
         CK_CUDA(cudaStreamSynchronize(s), "synchronise");
         for (int32_t i = 0; i < b->nmat; ++i) {
             if (!X[i] || !Y[i] || X[i] == Y[i]) return fail(CSRK_ERR_ARG, "bad vector pointer");
-            b->h_pinned_mats[i] = b->h_mats[i];
-            b->h_pinned_mats[i].X = X[i];
-            b->h_pinned_mats[i].Y = Y[i];
+            pinned[i] = b->h_mats[i];
+            if (xt && b->hs[i]->dtype == CSRK_F64) {
+                pinned[i].vals = b->hs[i]->d_vals[csrk::VAL_F32];
+                pinned[i].vt = csrk::VAL_F32;
+            }
+            pinned[i].xt = xt;
+            pinned[i].X = X[i];
+            pinned[i].Y = Y[i];
+            pinned[i].vec = ((uintptr_t)X[i] % 16 == 0) && ((uintptr_t)Y[i] % 16 == 0);
         }
-        CK_CUDA(cudaMemcpyAsync(b->d_mats_user, b->h_pinned_mats, b->nmat * sizeof(BatchMat),
-                                cudaMemcpyHostToDevice, s), "bind vectors");
-        b->bound_x.assign(X, X + b->nmat);
-        b->bound_y.assign(Y, Y + b->nmat);
+        CK_CUDA(cudaMemcpyAsync(table, pinned, b->nmat * sizeof(BatchMat), cudaMemcpyHostToDevice, s),
+                "bind vectors");
+        bx.assign(X, X + b->nmat);
+        by.assign(Y, Y + b->nmat);
     }
-    return launch_batch_spmm(b, b->d_mats_user, alpha, beta, s);
+    return launch_batch_spmm(b, table, alpha, beta, s);
 }
 
 }  // extern "C"

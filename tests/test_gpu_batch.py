@@ -103,6 +103,47 @@ def test_batch_spmm_matches_oracle_and_replays(budget, monkeypatch):
         csrk.destroy(h)
 
 
+@pytest.mark.parametrize("fp32", [False, True])
+@pytest.mark.parametrize("aligned", [True, False])
+def test_batch_spmm_vector_and_scalar_paths(fp32, aligned):
+    """Power-of-two k on 16-byte aligned blocks take the vector-load row routines; views one
+    element off a 16-byte boundary take the scalar ones.  FP32 mode: FP32 vectors and
+    accumulation on the values rounded to FP32 (BF16 stays BF16)."""
+    specs = [s for s in SPECS if s[2] != 33] + [(synth.stencil_3d(9, 8, 7, 27, "random_dd", 12), "f64", 32, (32, 2))]
+    hs, forms = make_batch(specs)
+    b = csrk.batch_create(hs, [k for _, _, k, _ in specs])
+    dt = torch.float32 if fp32 else torch.float64
+    flags = csrk.VEC_PERMUTED | (csrk.X_F32 | csrk.ACC_F32 if fp32 else 0)
+    Xs, Ys, bufs = [], [], []
+    for i, (a, _, k, _) in enumerate(specs):
+        X = synth.uniform_block(a.n, k, 800 + i)
+        if fp32:
+            X = precision.to_f32(X).astype(np.float64)          # exactly representable in FP32
+        off = 0 if aligned else 1
+        bx = torch.zeros(a.n * k + 4, dtype=dt, device=DEV)
+        by = torch.full((a.n * k + 4,), np.nan, dtype=dt, device=DEV)
+        bx[off:off + a.n * k] = torch.tensor(X.ravel(), dtype=dt, device=DEV)
+        Xs.append(bx[off:off + a.n * k].view(a.n, k))
+        Ys.append(by[off:off + a.n * k].view(a.n, k))
+        bufs.append((bx, by))
+    csrk.batch_spmm(b, 1.0, Xs, 0.0, Ys, flags=flags)
+    torch.cuda.synchronize()
+    for i, ((a, dtype, k, _), (rp, ci, v)) in enumerate(zip(specs, forms)):
+        X = Xs[i].double().cpu().numpy()
+        got = Ys[i].double().cpu().numpy()
+        vv = v if not fp32 or dtype == "bf16" else precision.to_f32(v).astype(np.float64)
+        ref = ospmv.csr_spmm(a.n, rp, ci, vv, X)
+        m = int(np.max(np.diff(rp)))
+        tol = (m + 2) * 2.0 ** -24 if fp32 else 1e-12
+        for c in range(k):
+            s_ = ospmv.abs_row_scale(rp, ci, vv, X[:, c])
+            assert np.all(np.abs(got[:, c] - ref[:, c]) <= tol * s_), (i, c)
+    assert csrk.batch_device_status(b) == 0
+    csrk.batch_destroy(b)
+    for h in hs:
+        csrk.destroy(h)
+
+
 def test_batch_spmm_many_items_per_block():
     """Enough items that every block's stage ring wraps many times (sampled rows)."""
     specs = [(synth.stencil_3d(64, 64, 64, 27, "random_dd", 21), "f64", 4, (32, 4)),
