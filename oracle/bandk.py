@@ -13,10 +13,12 @@ library) for k = 3 -- rows, super-rows (SR), super-super-rows (SSR):
        (component starts, pseudo-peripheral search, neighbours by (degree, index)), not
        reversed.  degree = number of distinct neighbours at that level.
   1.   Coarsen G0 -> G1: walk CM(G0); each still unassigned vertex seeds a new aggregate,
-       grown breadth-first from the seed (a dequeued member adds its unassigned
-       neighbours in (degree, index) order) until it holds `sr` vertices or no
-       unassigned neighbour is left.  Aggregates are numbered in creation order.  G1 has
-       an edge between two aggregates with weight = the number of G0 edges between them.
+       which grows one vertex at a time by the unassigned vertex adjacent to it with the
+       fewest unassigned neighbours (the one most at risk of being stranded), then the
+       largest edge weight into the aggregate, then the smallest index -- until it holds
+       `sr` vertices or nothing unassigned touches it.  Aggregates are numbered in
+       creation order.  G1 has an edge between two aggregates with weight = the number of
+       G0 edges between them.
   2.   Coarsen G1 -> G2 the same way with CM(G1) and cap `ssr` (counted in G1 vertices).
   3.   Order G2 by weighted reverse Cuthill-McKee: CM with the dequeued vertex's neighbours
        taken by (edge weight descending, degree, index), then reversed.
@@ -74,26 +76,33 @@ def _cm_sequence(n, adj, deg, nb_key):
     return seq
 
 
-def _aggregate(n, adj, deg, seeds, cap):
-    """Step 1 / 2: breadth-first aggregates of at most cap vertices, seeded in order."""
+def _aggregate(n, nbw, seeds, cap):
+    """Steps 1 / 2: aggregates of at most cap vertices, seeded in order; each grows by the
+    adjacent unassigned vertex with the fewest unassigned neighbours, then the largest edge
+    weight into the aggregate, then the smallest index."""
     agg = [-1] * n
+    free = [len(d) for d in nbw]          # unassigned neighbours of each vertex
     groups = []
+
+    def take(v, g, conn):
+        agg[v] = g
+        conn.pop(v, None)
+        for u, w in nbw[v].items():
+            free[u] -= 1
+            if agg[u] < 0:
+                conn[u] = conn.get(u, 0) + w
+
     for s in seeds:
         if agg[s] >= 0:
             continue
         g = len(groups)
         members = [s]
-        agg[s] = g
-        queue = [s]
-        head = 0
-        while head < len(queue) and len(members) < cap:
-            u = queue[head]
-            head += 1
-            for v in sorted(adj[u], key=lambda v: (deg[v], v)):
-                if agg[v] < 0 and len(members) < cap:
-                    agg[v] = g
-                    members.append(v)
-                    queue.append(v)
+        conn = {}
+        take(s, g, conn)
+        while len(members) < cap and conn:
+            v = min(conn, key=lambda u: (free[u], -conn[u], u))
+            members.append(v)
+            take(v, g, conn)
         groups.append(members)
     return agg, groups
 
@@ -192,13 +201,13 @@ def bandk_py(n, rowptr, colidx, sr, ssr):
     deg0 = [len(a) for a in adj0]
     nbw0 = [{u: 1 for u in a} for a in adj0]
     seeds0 = _cm_sequence(n, adj0, deg0, lambda v, u: (deg0[u], u))
-    agg1, groups1 = _aggregate(n, adj0, deg0, seeds0, sr)
+    agg1, groups1 = _aggregate(n, nbw0, seeds0, sr)
     n1 = len(groups1)
     nbw1 = _coarse_graph(nbw0, agg1, n1)
     adj1 = [sorted(d) for d in nbw1]
     deg1 = [len(a) for a in adj1]
     seeds1 = _cm_sequence(n1, adj1, deg1, lambda v, u: (deg1[u], u))
-    agg2, groups2 = _aggregate(n1, adj1, deg1, seeds1, ssr)
+    agg2, groups2 = _aggregate(n1, nbw1, seeds1, ssr)
     n2 = len(groups2)
     nbw2 = _coarse_graph(nbw1, agg2, n2)
     adj2 = [sorted(d) for d in nbw2]
