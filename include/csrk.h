@@ -95,9 +95,9 @@ int csrk_create(int32_t n, const int32_t* rowptr, const int32_t* colidx, const d
                 csrk_dtype dtype, csrk_handle* out);
 
 /* csrk_reorder: renumber rows and columns by a bandwidth-reducing permutation so that a
- * super-row's rows share x entries (Sec. 2.1 RCM; the paper's own Band-k ordering,
- * Listing 2, is not implemented).  B = P A P^T with B[i][j] = A[perm[i]][perm[j]], each
- * row's columns ascending.
+ * super-row's rows share x entries (Sec. 2.1 RCM; for the paper's own Band-k ordering,
+ * Listing 2, see csrk_reorder_bandk).  B = P A P^T with B[i][j] = A[perm[i]][perm[j]],
+ * each row's columns ascending.
  *   method    CSRK_REORDER_NONE or CSRK_REORDER_RCM
  *   perm_out  optional host array of n entries receiving perm (perm[new] = old)
  * RCM reading: graph of A + A^T without self-loops; each component starts at the
@@ -108,6 +108,30 @@ int csrk_create(int32_t n, const int32_t* rowptr, const int32_t* colidx, const d
  * Errors: CSRK_ERR_STATE after the pointers exist, CSRK_ERR_ARG, CSRK_ERR_ALLOC.
  * Host only. */
 int csrk_reorder(csrk_handle h, int method, int32_t* perm_out);
+
+/* csrk_reorder_bandk: the Band-k ordering for k = 3 (Sec. 2.3, Listing 2, Fig. 2): the
+ * rows are coarsened into super-rows of at most sr rows and those into super-super-rows
+ * of at most ssr super-rows, the coarse levels are put in weighted bandwidth-limiting
+ * order and expanded again; the renumbering and the (variable) pointer arrays are
+ * installed together, so no csrk_set_sizes / csrk_set_pointers call is needed after it.
+ *   sr, ssr   caps, >= 1
+ *   perm_out  optional host array of n entries receiving perm (perm[new] = old),
+ *             composed with any earlier csrk_reorder
+ * Reading (the paper names neither coarsening nor weights): graph of A + A^T without
+ * self-loops, edge weights 1.  Coarsen: walk the Cuthill-McKee sequence (csrk_reorder's
+ * rules, not reversed); each unassigned vertex seeds an aggregate grown breadth-first
+ * (neighbours by degree, index) to the cap; the coarse edge weight is the number of fine
+ * edges between two aggregates.  The coarsest graph is ordered by weighted reverse
+ * Cuthill-McKee (neighbours by weight descending, degree, index).  Expansion orders each
+ * coarse node's members by a breadth-first walk inside the node (same neighbour key) from
+ * the member most connected to what is already placed, else from the member farthest from
+ * the node's boundary (ties: smaller outside weight, index), else from the node's
+ * pseudo-peripheral vertex.  csrk_set_sizes(h, 0, 0) afterwards tunes the launch shape
+ * only and keeps these pointers; csrk_set_sizes with explicit sizes replaces them (the
+ * row order stays).
+ * Errors: CSRK_ERR_STATE after the pointers exist, CSRK_ERR_ARG, CSRK_ERR_ALLOC.
+ * Host only. */
+int csrk_reorder_bandk(csrk_handle h, int32_t sr, int32_t ssr, int32_t* perm_out);
 
 /* csrk_set_sizes: build sr_ptr / ssr_ptr for fixed sizes (Sec. 2.2): every super-row
  * holds sr rows and every super-super-row ssr super-rows, the last of each possibly

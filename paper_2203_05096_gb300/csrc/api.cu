@@ -539,17 +539,23 @@ float time_launches(csrk_matrix* h, cudaStream_t s, cudaEvent_t e0, cudaEvent_t 
 
 int autotune(csrk_matrix* h) {
     int rc;
-    if (h->m.n == 0) return set_fixed(h, 32, 8);
+    // Band-k pointers in place: tune the launch shape only, on those pointers
+    const bool bandk = h->have_ptrs && h->bandk_sr > 0;
+    if (h->m.n == 0) return bandk ? CSRK_OK : set_fixed(h, 32, 8);
     if ((rc = ensure_context(h))) return rc;
     // sizes first so that the key can see the longest row
-    if ((rc = set_fixed(h, 32, 8))) return rc;
-    const std::string key = tune_key(h);
+    if (!bandk && (rc = set_fixed(h, 32, 8))) return rc;
+    const std::string key = tune_key(h) + (bandk ? ":bandk" + std::to_string(h->bandk_sr) + "x" +
+                                                       std::to_string(h->bandk_ssr)
+                                                 : std::string());
+    // (re)install the chosen sizes; Band-k keeps its own pointers
+    auto install = [&](int32_t sr, int32_t ssr) { return bandk ? CSRK_OK : set_fixed(h, sr, ssr); };
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         load_tune_file();
         for (auto& e : g_tune_cache)
             if (e.first == key) {
-                if ((rc = set_fixed(h, e.second.sr, e.second.ssr))) return rc;
+                if ((rc = install(e.second.sr, e.second.ssr))) return rc;
                 h->cfg = e.second.cfg;
                 h->cfg_set = true;
                 h->kernel_forced = false;
@@ -581,8 +587,9 @@ int autotune(csrk_matrix* h) {
     std::vector<TunedChoice> phase1;
     h->cfg_set = false;
     h->kernel_forced = false;
+    if (bandk) sizes.assign(1, {0, 0});
     for (auto& sz : sizes) {
-        if ((rc = set_fixed(h, sz.first, sz.second))) break;
+        if ((rc = install(sz.first, sz.second))) break;
         if ((rc = ensure_struct(h))) break;
         TunedChoice c;
         c.sr = sz.first;
@@ -601,7 +608,7 @@ int autotune(csrk_matrix* h) {
     else pairs = {{4, 8}, {8, 8}, {32, 4}};
     const bool with_pairs = pairs_available(h);
     for (size_t b = 0; b < std::min<size_t>(3, phase1.size()) && rc == CSRK_OK; ++b) {
-        if ((rc = set_fixed(h, phase1[b].sr, phase1[b].ssr)) || (rc = ensure_struct(h))) break;
+        if ((rc = install(phase1[b].sr, phase1[b].ssr)) || (rc = ensure_struct(h))) break;
         for (auto& pr : pairs)
             for (int warps : {8, 16})
                 for (int kernel : {0, 1, 2, 3})
@@ -631,8 +638,8 @@ int autotune(csrk_matrix* h) {
     cudaEventDestroy(e1);
     cudaStreamDestroy(s);
     if (rc) return rc;
-    if (best.sr <= 0) return fail(CSRK_ERR_CUDA, "autotuning found no working configuration");
-    if ((rc = set_fixed(h, best.sr, best.ssr))) return rc;
+    if (phase1.empty() || best.us >= 1e29f) return fail(CSRK_ERR_CUDA, "autotuning found no working configuration");
+    if ((rc = install(best.sr, best.ssr))) return rc;
     h->cfg = best.cfg;
     h->cfg_set = true;
     h->kernel_forced = false;
@@ -700,6 +707,36 @@ int csrk_reorder(csrk_handle h, int method, int32_t* perm_out) {
     return CSRK_OK;
 }
 
+int csrk_reorder_bandk(csrk_handle h, int32_t sr, int32_t ssr, int32_t* perm_out) {
+    if (!h) return fail(CSRK_ERR_ARG, "handle is NULL");
+    if (h->have_ptrs) return fail(CSRK_ERR_STATE, "reorder must come before csrk_set_sizes / csrk_set_pointers");
+    if (sr < 1 || ssr < 1) return fail(CSRK_ERR_ARG, "sr and ssr must be >= 1");
+    try {
+        std::vector<int32_t> local, srp, ssrp;
+        bandk_permutation(h->m, sr, ssr, local, srp, ssrp);
+        CsrHost b;
+        permute_symmetric(h->m, local, b);
+        h->m = std::move(b);
+        if (!h->perm.empty())
+            for (auto& p : local) p = h->perm[p];
+        h->perm = std::move(local);
+        if (perm_out) {
+            if (h->perm.empty())
+                for (int32_t i = 0; i < h->m.n; ++i) perm_out[i] = i;
+            else
+                std::memcpy(perm_out, h->perm.data(), sizeof(int32_t) * h->perm.size());
+        }
+        int rc = install_pointers_impl(h, std::move(srp), std::move(ssrp));
+        if (rc) return rc;
+    } catch (const std::bad_alloc&) {
+        return fail(CSRK_ERR_ALLOC, "out of host memory");
+    }
+    h->sr = h->ssr = 0;
+    h->bandk_sr = sr;
+    h->bandk_ssr = ssr;
+    return CSRK_OK;
+}
+
 }  // extern "C"
 
 namespace {
@@ -738,6 +775,7 @@ int csrk_set_sizes(csrk_handle h, int32_t sr, int32_t ssr) {
     }
     h->sr = sr;
     h->ssr = ssr;
+    h->bandk_sr = h->bandk_ssr = 0;
     return CSRK_OK;
 }
 
@@ -753,6 +791,7 @@ int csrk_set_pointers(csrk_handle h, int32_t nsr, const int32_t* sr_ptr, int32_t
         return fail(CSRK_ERR_ALLOC, "out of host memory");
     }
     h->sr = h->ssr = 0;
+    h->bandk_sr = h->bandk_ssr = 0;
     return CSRK_OK;
 }
 

@@ -43,6 +43,9 @@ int ingest_csr(int32_t n, const int32_t* rowptr, const int32_t* colidx, const do
                CsrHost& out, std::string& err);
 // Reverse Cuthill-McKee permutation, perm[new] = old.
 void rcm_permutation(const CsrHost& a, std::vector<int32_t>& perm);
+// Band-k (k = 3) ordering and its variable super-row / super-super-row pointers.
+void bandk_permutation(const CsrHost& a, int32_t sr, int32_t ssr, std::vector<int32_t>& perm,
+                       std::vector<int32_t>& sr_ptr, std::vector<int32_t>& ssr_ptr);
 // B = P A P^T, rows' columns ascending.
 void permute_symmetric(const CsrHost& a, const std::vector<int32_t>& perm, CsrHost& b);
 void fixed_pointers(int32_t n, int32_t sr, int32_t ssr, std::vector<int32_t>& sr_ptr,

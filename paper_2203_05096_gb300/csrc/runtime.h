@@ -22,6 +22,7 @@ struct csrk_matrix {
     csrk_dtype dtype = CSRK_F64;
     bool have_ptrs = false;
     int32_t sr = 0, ssr = 0;       // fixed sizes (0 when given explicitly)
+    int32_t bandk_sr = 0, bandk_ssr = 0;   // caps of the Band-k pointers in place (0: none)
     std::vector<int32_t> sr_ptr, ssr_ptr;
     std::vector<SsrDesc> desc;
     TileStats stats;

@@ -43,6 +43,7 @@ _pi64 = ctypes.POINTER(ctypes.c_int64)
 _PROTOS = {
     "csrk_create": [_i32, _vp, _vp, _vp, ctypes.c_int, ctypes.POINTER(_vp)],
     "csrk_reorder": [_vp, ctypes.c_int, _vp],
+    "csrk_reorder_bandk": [_vp, _i32, _i32, _vp],
     "csrk_set_sizes": [_vp, _i32, _i32],
     "csrk_set_pointers": [_vp, _i32, _vp, _i32, _vp],
     "csrk_spmv": [_vp, _d, _vp, _d, _vp, _u, _vp],
@@ -143,6 +144,15 @@ def reorder(h, method="rcm", want_perm=True):
     perm = np.empty(n, dtype=np.int32) if want_perm else None
     _check(lib().csrk_reorder(h, REORDER[method], None if perm is None else perm.ctypes.data_as(_vp)),
            "csrk_reorder")
+    return perm
+
+
+def reorder_bandk(h, sr, ssr, want_perm=True):
+    """Band-k ordering with its variable super-row / super-super-row pointers."""
+    n = info(h)["n"]
+    perm = np.empty(n, dtype=np.int32) if want_perm else None
+    _check(lib().csrk_reorder_bandk(h, int(sr), int(ssr), None if perm is None else perm.ctypes.data_as(_vp)),
+           "csrk_reorder_bandk")
     return perm
 
 

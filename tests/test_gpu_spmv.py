@@ -418,3 +418,47 @@ def test_pair_path_refused_for_out_of_range_values():
     csrk.set_config(h, kernel=0)
     assert_close(gpu_spmv(h, x), a, a.vals, x)
     csrk.destroy(h)
+
+
+# ------------------------------------------------------------------ Band-k pointers
+BANDK_GPU = [
+    ("stencil27", lambda: small_27pt(17), (32, 4)),
+    ("stencil7", lambda: synth.stencil_3d(30, 20, 11, 7, "random_dd", 18, labels=synth.vectors.permutation(6600, 18)), (32, 8)),
+    ("fem", lambda: synth.fem_like(12, 19), (16, 3)),
+    ("random", lambda: synth.random_pattern(3000, 0.003, 20, symmetric=True, empty_rows=25), (8, 5)),
+]
+
+
+@pytest.mark.parametrize("name,make,caps", BANDK_GPU, ids=[c[0] for c in BANDK_GPU])
+@pytest.mark.parametrize("kernel", [0, 1])
+def test_bandk_pointers_spmv(name, make, caps, kernel):
+    """Variable super-rows and super-super-rows from Band-k, natural-numbering SpMV (fused
+    unpermute) and the reordered-numbering form, TMA-staged and direct-load kernels."""
+    a = make()
+    h = csrk.create(a.n, a.rowptr, a.colidx, a.vals)
+    perm = csrk.reorder_bandk(h, *caps)
+    csrk.set_config(h, kernel=kernel, lanes=1, unroll=8, warps=8)
+    x = synth.uniform_vector(a.n, 31)
+    y0 = synth.uniform_vector(a.n, 32)
+    assert_close(gpu_spmv(h, x, 1.5, -0.25, y0), a, a.vals, x, 1.5, -0.25, y0)
+    e = csrk.export(h)
+    b = synth.CSR(a.n, e["rowptr"], e["colidx"], e["vals"])
+    assert_close(gpu_spmv(h, x[perm], flags=csrk.VEC_PERMUTED), b, b.vals, x[perm])
+    csrk.destroy(h)
+
+
+def test_bandk_autotune_keeps_pointers():
+    a = small_27pt(21)
+    h = csrk.create(a.n, a.rowptr, a.colidx, a.vals)
+    csrk.reorder_bandk(h, 32, 4)
+    before = csrk.export(h)
+    csrk.set_sizes(h, 0, 0)
+    after = csrk.export(h)
+    assert np.array_equal(before["sr_ptr"], after["sr_ptr"]) and np.array_equal(before["ssr_ptr"], after["ssr_ptr"])
+    assert csrk.info(h)["sr"] == 0
+    x = synth.uniform_vector(a.n, 33)
+    assert_close(gpu_spmv(h, x), a, a.vals, x)
+    csrk.set_sizes(h, 32, 8)                          # explicit sizes replace them; the order stays
+    assert np.array_equal(csrk.export(h)["perm"], before["perm"]) and csrk.info(h)["sr"] == 32
+    assert_close(gpu_spmv(h, x), a, a.vals, x)
+    csrk.destroy(h)

@@ -107,3 +107,65 @@ def test_model_sizes_hand_worked():
         arch, r = head.split()
         assert csrk.model_sizes(float(r), arch) == tuple(int(v) for v in expect.split()), head
         assert csrk.model_sizes(float(r), arch) == tuning.model_sizes(float(r), arch)
+
+
+# ------------------------------------------------------------------ Band-k
+BANDK_CASES = [
+    ("grid2d", lambda: synth.stencil_2d_5pt(17, 13)),
+    ("grid2d_scrambled", lambda: synth.relabel(synth.stencil_2d_5pt(17, 13), synth.vectors.permutation(221, 5))),
+    ("stencil27", lambda: synth.stencil_3d(7, 6, 5, 27, "random_dd", 2, labels=synth.vectors.permutation(210, 2))),
+    ("fem", lambda: synth.fem_like(6, 3)),
+    ("components", lambda: synth.random_pattern(300, 0.01, 4, symmetric=True, empty_rows=7)),
+    ("nonsymmetric", lambda: synth.random_pattern(200, 0.02, 9, symmetric=False)),
+]
+
+
+@pytest.mark.parametrize("name,make", BANDK_CASES, ids=[c[0] for c in BANDK_CASES])
+@pytest.mark.parametrize("sr,ssr", [(8, 4), (32, 8), (1, 1), (5, 3)])
+def test_bandk_bit_exact_against_oracle(name, make, sr, ssr):
+    from oracle import bandk
+    a = make()
+    h = csrk.create(a.n, a.rowptr, a.colidx, a.vals)
+    perm = csrk.reorder_bandk(h, sr, ssr)
+    e = csrk.export(h)
+    p_ref, sr_ref, ssr_ref = bandk.bandk_py(a.n, a.rowptr, a.colidx, sr, ssr)
+    assert np.array_equal(perm, p_ref) and np.array_equal(e["perm"], p_ref)
+    assert np.array_equal(e["sr_ptr"], sr_ref) and np.array_equal(e["ssr_ptr"], ssr_ref)
+    # the matrix is B = P A P^T under that permutation
+    rp, ci, v = reorder.permute_loop(a.n, a.rowptr, a.colidx, a.vals, p_ref)
+    assert np.array_equal(e["rowptr"], rp) and np.array_equal(e["colidx"], ci) and np.array_equal(e["vals"], v)
+    csrk.destroy(h)
+
+
+def test_bandk_state_and_arguments():
+    a = synth.stencil_2d_5pt(8, 8)
+    h = csrk.create(a.n, a.rowptr, a.colidx, a.vals)
+    for sr, ssr in [(0, 4), (4, 0), (-1, 2)]:
+        with pytest.raises(csrk.CsrkError) as ei:
+            csrk.reorder_bandk(h, sr, ssr)
+        assert ei.value.status == "ERR_ARG"
+    csrk.reorder(h)                                   # composes with an earlier RCM
+    p_rcm = csrk.export(h, with_pointers=False)["perm"].copy()
+    perm = csrk.reorder_bandk(h, 8, 2)
+    rcm_form = csrk.create(a.n, *reorder.permute_loop(a.n, a.rowptr, a.colidx, a.vals, p_rcm))
+    from oracle import bandk
+    local, _, _ = bandk.bandk_py(a.n, *reorder.permute_loop(a.n, a.rowptr, a.colidx, a.vals, p_rcm)[:2], 8, 2)
+    assert np.array_equal(perm, p_rcm[local])
+    with pytest.raises(csrk.CsrkError) as ei:        # pointers exist: no further reorder
+        csrk.reorder_bandk(h, 8, 2)
+    assert ei.value.status == "ERR_STATE"
+    csrk.destroy(rcm_form)
+    csrk.destroy(h)
+
+
+def test_bandk_large_stencil_invariants():
+    a = synth.stencil_3d(40, 40, 40, 7, "random_dd", 9, labels=synth.vectors.permutation(64000, 9))
+    h = csrk.create(a.n, a.rowptr, a.colidx, a.vals)
+    perm = csrk.reorder_bandk(h, 32, 4)
+    e = csrk.export(h)
+    assert np.array_equal(np.sort(perm), np.arange(a.n))
+    assert np.all(np.diff(e["sr_ptr"]) >= 1) and np.all(np.diff(e["sr_ptr"]) <= 32)
+    assert np.all(np.diff(e["ssr_ptr"]) >= 1) and np.all(np.diff(e["ssr_ptr"]) <= 4)
+    # most super-rows are full: the aggregates pack the grid
+    assert np.mean(np.diff(e["sr_ptr"])) > 24
+    csrk.destroy(h)
