@@ -212,7 +212,12 @@ def run_ours(args, world, rank, local):
     state = []
     for name, a in mats:
         h = csrk.create(a.n, a.rowptr, a.colidx, a.vals, args.dtype)
-        csrk.reorder(h, "rcm", want_perm=False)
+        t_order = time.perf_counter()
+        if args.ordering == "bandk":      # Band-k with its own variable SR / SSR pointers
+            csrk.reorder_bandk(h, *(int(v) for v in args.bandk_caps.split(",")), want_perm=False)
+        else:
+            csrk.reorder(h, "rcm", want_perm=False)
+        t_order = time.perf_counter() - t_order
         t_tune = time.perf_counter()
         if args.sizes == "auto":
             csrk.set_sizes(h, 0, 0)          # the library's autotuner (timed on this matrix)
@@ -225,7 +230,7 @@ def run_ours(args, world, rank, local):
         x = torch.tensor(synth.uniform_vector(a.n, 2), dtype=torch.float64, device=dev)
         xp, yp, y = torch.empty_like(x), torch.empty_like(x), torch.empty_like(x)
         state.append(dict(name=name, a=a, h=h, info=inf, x=x, xp=xp, yp=yp, y=y,
-                          cfg=csrk.tuned_config(h), tune_s=t_tune))
+                          cfg=csrk.tuned_config(h), tune_s=t_tune, order_s=t_order))
 
     perm_fn, spmv_fn = lib.csrk_permute, lib.csrk_spmv
     XP = csrk.X_PERMUTED   # x in the reordered numbering, y stored to its input place
@@ -314,8 +319,9 @@ def run_ours(args, world, rank, local):
                                  "kernel_gbs": round(b / (km * 1e-3) / 1e9, 1),
                                  "kernel_frac_of_peak": round(b / (km * 1e-3) / 1e9 / peak, 3),
                                  "permute_us": round(statistics.mean(perm_ms[j]) * 1e3, 2),
-                                 "sr": inf["sr"], "ssr": inf["ssr"], "config": s["cfg"],
-                                 "setup_s": round(s["tune_s"], 2)}
+                                 "sr": inf["sr"], "ssr": inf["ssr"], "nsr": inf["nsr"], "nssr": inf["nssr"],
+                                 "config": s["cfg"],
+                                 "setup_s": round(s["tune_s"], 2), "order_s": round(s["order_s"], 2)}
 
     # end to end: the public call with host vectors (pinned), copies inside the timed region
     e2e = None
@@ -396,7 +402,8 @@ def run_ours(args, world, rank, local):
             "config": {"workload": WORKLOAD,
                        "method": "CSR-3 sizes and launch shape from the library autotuner; per matrix "
                                  "permute x, then the CSR-3 kernel storing y in the input numbering",
-                       "sizes": args.sizes, "l2": "inputs larger than L2 (~930 MB per step vs 129 MB)",
+                       "sizes": args.sizes, "ordering": args.ordering if args.ordering == "rcm" else
+                       f"bandk {args.bandk_caps}", "l2": "inputs larger than L2 (~930 MB per step vs 129 MB)",
                        "parallelism": f"replicas x{world}", "per_matrix": per_matrix},
             "roofline": {"bound": "hbm", "kernel": f"csr3 {state[dom]['name']}",
                          "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
@@ -598,6 +605,9 @@ def main():
     p.add_argument("--no-batch", action="store_true")
     p.add_argument("--side", type=int, default=SIDE, help="grid side (profiling runs use a smaller case)")
     p.add_argument("--only", choices=[m for m, _ in MATRICES], default=None)
+    p.add_argument("--ordering", choices=("rcm", "bandk"), default="rcm",
+                   help="row ordering: RCM with fixed sizes, or Band-k with its own pointers")
+    p.add_argument("--bandk-caps", default="32,4", help="Band-k caps 'sr,ssr'")
     p.add_argument("--batch-only", action="store_true",
                    help="run only the batched section (profiling); prints {'batch': ...}")
     args = p.parse_args()
