@@ -47,11 +47,11 @@ WORKLOAD = ("128^3 7-point and 27-point random diagonally dominant stencils (FP6
 SR, SSR = 32, 8
 MATRICES = (("stencil7", 7), ("stencil27", 27))
 
-# DRAM traffic per launch of the dominant kernel from an ncu capture, valid only for the
-# kernel source it was taken on.  The 27-point entry is the 96^3 capture summarised in
+# DRAM traffic per launch of the dominant kernel from an ncu capture, keyed by (matrix,
+# dtype, kernel number) and valid only for the kernel source it was taken on.  The 27-point entry is the 96^3 capture summarised in
 # profiles/csr3_tma_27pt_96cubed_f64.md (299.20 MB) scaled to 128^3 by nonzeros.
 NCU_TRAFFIC = {
-    ("stencil27", "f64"): {"bytes": 712_940_980, "kernel_hash": "871b5d682a86"},
+    ("stencil27", "f64", 0): {"bytes": 712_940_980, "kernel_hash": "871b5d682a86"},
 }
 
 
@@ -105,12 +105,17 @@ def build_matrices(side=SIDE, only=None):
     return out
 
 
-def alg_bytes_spmv(n, nnz, nsr, nssr, val_bytes=8, x_bytes=8, fused_unpermute=True):
-    # every stored value and column index, rowptr, sr_ptr, the 32-byte SSR descriptors,
-    # x read once and y written once (beta = 0), and the permutation read once when the
-    # kernel stores y in the input numbering
-    return ((val_bytes + 4) * nnz + 4 * (n + 1) + 4 * (nsr + 1) + 32 * nssr + x_bytes * n + x_bytes * n
+def alg_bytes_spmv(n, nnz, nsr, nssr, val_bytes=8, x_bytes=8, fused_unpermute=True, col_bytes=4):
+    # every stored value and column index (4 bytes, or a 2-byte offset with kernel 4),
+    # rowptr, sr_ptr, the 32-byte SSR descriptors, x read once and y written once
+    # (beta = 0), and the permutation read once when the kernel stores y in the input
+    # numbering
+    return ((val_bytes + col_bytes) * nnz + 4 * (n + 1) + 4 * (nsr + 1) + 32 * nssr + x_bytes * n + x_bytes * n
             + (4 * n if fused_unpermute else 0))
+
+
+def col_bytes_of(cfg):
+    return 2 if cfg.get("kernel") == 4 else 4
 
 
 class ClockSampler:
@@ -301,18 +306,18 @@ def run_ours(args, world, rank, local):
     dom = max(range(len(state)), key=lambda j: statistics.mean(kern_ms[j]))
     sd = state[dom]
     inf = sd["info"]
-    abytes = alg_bytes_spmv(inf["n"], inf["nnz"], inf["nsr"], inf["nssr"], vb)
+    abytes = alg_bytes_spmv(inf["n"], inf["nnz"], inf["nsr"], inf["nssr"], vb, col_bytes=col_bytes_of(sd["cfg"]))
     kmean = statistics.mean(kern_ms[dom])
     achieved = abytes / (kmean * 1e-3) / 1e9
     khash = kernel_source_hash()
-    tr = NCU_TRAFFIC.get((sd["name"], args.dtype))
+    tr = NCU_TRAFFIC.get((sd["name"], args.dtype, sd["cfg"]["kernel"]))
     traffic = tr["bytes"] if tr and tr["kernel_hash"] == khash else None
 
     per_matrix = {}
     for j, s in enumerate(state):
         inf = s["info"]
         km = statistics.mean(kern_ms[j])
-        b = alg_bytes_spmv(inf["n"], inf["nnz"], inf["nsr"], inf["nssr"], vb)
+        b = alg_bytes_spmv(inf["n"], inf["nnz"], inf["nsr"], inf["nssr"], vb, col_bytes=col_bytes_of(s["cfg"]))
         per_matrix[s["name"]] = {"n": inf["n"], "nnz": inf["nnz"], "kernel_us": round(km * 1e3, 2),
                                  "kernel_min_us": round(min(kern_ms[j]) * 1e3, 2),
                                  "kernel_gflops": round(2.0 * inf["nnz"] / (km * 1e-3) / 1e9, 1),
@@ -362,10 +367,14 @@ def run_ours(args, world, rank, local):
             csrk.cg(s27["h"], b, xs, 1e-10, 5000, inner, 20, restart)     # capture the graphs
             torch.cuda.synchronize()
             times = []
-            for _ in range(3):
+            for rep in range(3):
                 c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 c0.record(stream)
+                if rep == 0:
+                    torch.cuda.nvtx.range_push(f"cg_{inner}")   # lets a profiler keep one solve
                 rc, iters, rel = csrk.cg(s27["h"], b, xs, 1e-10, 5000, inner, 20, restart)
+                if rep == 0:
+                    torch.cuda.nvtx.range_pop()
                 c1.record(stream)
                 torch.cuda.synchronize()
                 times.append(c0.elapsed_time(c1))

@@ -141,6 +141,12 @@ int csrk_reorder_bandk(csrk_handle h, int32_t sr, int32_t ssr, int32_t* perm_out
  * Host only for explicit sizes. */
 int csrk_set_sizes(csrk_handle h, int32_t sr, int32_t ssr);
 
+/* csrk_index_bits: 16 when the columns fit kernel 4's delta coding -- within each row, the
+ * first column minus its super-super-row's smallest column, and every step from one column
+ * to the next, at most 65,535 -- then kernel 4 (csrk_set_config) reads 2 bytes per nonzero
+ * instead of 4; else 32.  Needs the pointer arrays (CSRK_ERR_STATE before).  Host only. */
+int csrk_index_bits(csrk_handle h, int32_t* bits);
+
 /* csrk_set_pointers: give the super-row and super-super-row pointer arrays explicitly
  * (variable sizes, e.g. Fig. 1: sr_ptr = {0,2,5,7,9}, ssr_ptr = {0,2,4}).
  *   nsr     number of super-rows; sr_ptr has nsr+1 entries, sr_ptr[0] = 0,
@@ -360,7 +366,10 @@ int csrk_model_sizes(double rdensity, int arch, int32_t* ssrs, int32_t* srs);
  *            sum |a_ij x_j| for rows up to 48 entries) on the FP32 pipes, which on GB300
  *            run 58x the FP64 FMA rate.  Available when every value is 0 or has magnitude
  *            in [2^-39, 2^60] and no row exceeds 48 entries; x entries outside that range
- *            are multiplied in FP64 individually.  SpMV only (SpMM uses 0 / 1)
+ *            are multiplied in FP64 individually.  SpMV only (SpMM uses 0 / 1);
+ *            4 = TMA-staged with delta-coded 16-bit columns (csrk_index_bits = 16;
+ *            lanes 1, unroll 4, 8 or 16; SpMV only, SpMM uses 0): 12 -> 10 bytes per FP64
+ *            nonzero, results identical to kernel 0
  *   lanes    lanes cooperating on one row (SpMV): 1, 2, 4, 8 or 32
  *   unroll   x gathers a lane issues before consuming them; compiled (lanes, unroll)
  *            pairs: (1,4) (1,8) (1,16) (1,32) (2,8) (2,16) (4,8) (8,8) (32,4)
@@ -375,10 +384,10 @@ int csrk_tuned_config(csrk_handle h, int32_t* kernel, int32_t* lanes, int32_t* u
 
 /* csrk_set_config: force a launch configuration (same fields as csrk_tuned_config; a
  * negative field keeps the current value; a new lanes value without an unroll picks the
- * default unroll for it).  When kernel = 0 is given explicitly and the super-super-rows
- * do not fit two shared-memory stages, the compute calls return CSRK_ERR_UNSUPPORTED;
- * otherwise such a shape falls back to the direct kernel.  Used by the autotuner and
- * tests. */
+ * default unroll for it).  When kernel = 0 (or 2, 4) is given explicitly and the
+ * super-super-rows do not fit two shared-memory stages, or kernel 2 / 4 is not available
+ * for the matrix, the compute calls return CSRK_ERR_UNSUPPORTED; otherwise such a shape
+ * falls back (to the direct kernel, or from 4 to 0).  Used by the autotuner and tests. */
 int csrk_set_config(csrk_handle h, int32_t kernel, int32_t lanes, int32_t unroll,
                     int32_t warps, int32_t stages, int32_t ctas);
 

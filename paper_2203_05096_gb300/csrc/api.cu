@@ -51,6 +51,9 @@ void free_struct(csrk_matrix* h) {
     free_ptrs(h);
     cudaFree(h->d_rowptr);
     cudaFree(h->d_colidx);
+    cudaFree(h->d_col16);
+    h->d_col16 = nullptr;
+    h->col16_ok = -1;
     cudaFree(h->d_perm);
     h->d_rowptr = h->d_colidx = h->d_perm = nullptr;
     h->dev_struct = false;
@@ -208,6 +211,22 @@ bool pairs_available(csrk_matrix* h) {
     return h->pairs_ok == 1;
 }
 
+// (lanes, unroll) pairs compiled with 16-bit column offsets (kernel 4).
+bool mode3_compiled(int lanes, int unroll) { return lanes == 1 && (unroll == 4 || unroll == 8 || unroll == 16); }
+
+// Delta-coded 16-bit columns (kernel 4) need every code to fit 16 bits; the coded array is
+// built and uploaded on the first ask for the current pointers.
+bool col16_available(csrk_matrix* h) {
+    if (h->col16_ok < 0) {
+        h->col16_ok = 0;
+        std::vector<uint16_t> tmp;
+        if (h->have_ptrs && compress_columns(h->m, h->desc, tmp) &&
+            upload_padded(&h->d_col16, tmp.data(), tmp.size(), 2, "col16") == CSRK_OK)
+            h->col16_ok = 1;
+    }
+    return h->col16_ok == 1;
+}
+
 int smem_budget(const csrk_matrix* h, int ctas) {
     int per_cta = h->smem_per_sm / std::max(1, ctas) - 1024;
     return std::min(per_cta, h->smem_optin);
@@ -216,12 +235,12 @@ int smem_budget(const csrk_matrix* h, int ctas) {
 }  // namespace rt
 }  // namespace csrk
 
-bool csrk::plan_stages(const TileStats& st, int val_bytes, int max_smem, int want_stages,
+bool csrk::plan_stages(const TileStats& st, int val_bytes, int max_smem, int want_stages, int col_bytes,
                        StagePlan& plan) {
     auto r16 = [](int64_t v) { return (v + 15) & ~int64_t(15); };
     const int64_t srp = r16((int64_t)(st.max_srs + 8) * 4);
     const int64_t rp = r16((int64_t)(st.max_rows + 8) * 4);
-    const int64_t col = r16((st.max_nnz + 8) * 4);
+    const int64_t col = r16((st.max_nnz + 32 / col_bytes) * col_bytes);   // slice rounded out to 16 B
     const int64_t val = r16((st.max_nnz + 16) * val_bytes);
     int64_t stage = srp + rp + col + val;
     stage = (stage + 127) & ~int64_t(127);
@@ -242,7 +261,7 @@ bool csrk::plan_stages(const TileStats& st, int val_bytes, int max_smem, int wan
 
 int csrk::launch_csr3(const LaunchArgs& a, const KernelConfig& cfg, const StagePlan& plan,
                       void* stream) {
-    if (cfg.kernel >= 2) return launch_csr3_ds(a, cfg, plan, stream);
+    if (cfg.kernel == 2 || cfg.kernel == 3) return launch_csr3_ds(a, cfg, plan, stream);
     switch (a.val_type) {
         case VAL_F64: return launch_csr3_f64(a, cfg, plan, stream);
         case VAL_F32: return launch_csr3_f32(a, cfg, plan, stream);
@@ -259,22 +278,36 @@ int resolve_config(csrk_matrix* h, int vt, KernelConfig& cfg, StagePlan& plan) {
     // (the inner SpMV of a mixed-precision solve) start from the default shape
     cfg = (h->cfg_set && vt == (int)h->dtype) ? h->cfg : default_config(h);
     plan = StagePlan{};
-    if (cfg.kernel >= 2 && (vt != VAL_F64 || !pairs_available(h))) {
-        if (h->kernel_forced && vt == (int)h->dtype)
+    const bool forced = h->kernel_forced && vt == (int)h->dtype;
+    // other value types (a mixed solve's inner product) take the 16-bit column coding
+    // whenever it fits: their bytes are mostly indices
+    if (vt != (int)h->dtype && cfg.kernel == 0 && mode3_compiled(cfg.lanes, cfg.unroll) && col16_available(h))
+        cfg.kernel = 4;
+    if ((cfg.kernel == 2 || cfg.kernel == 3) && (vt != VAL_F64 || !pairs_available(h))) {
+        if (forced)
             return fail(CSRK_ERR_UNSUPPORTED, "the FP32-pair FP64 path needs FP64 values in [2^-39, 2^60] "
                                               "and rows of at most 48 entries");
         cfg.kernel -= 2;
     }
-    if (cfg.kernel >= 2 && cfg.unroll != 4 && cfg.unroll != 8 && cfg.unroll != 16) cfg.unroll = 8;
+    if (cfg.kernel == 4 && (!col16_available(h) || !mode3_compiled(cfg.lanes, cfg.unroll))) {
+        if (forced)
+            return fail(CSRK_ERR_UNSUPPORTED, "16-bit columns need every row's first column within 65,535 "
+                                              "of its SSR's smallest and every step between a row's columns "
+                                              "at most 65,535; lanes 1 and unroll 4, 8 or 16");
+        cfg.kernel = 0;
+    }
+    if ((cfg.kernel == 2 || cfg.kernel == 3) && cfg.unroll != 4 && cfg.unroll != 8 && cfg.unroll != 16)
+        cfg.unroll = 8;
+    const bool staged = cfg.kernel == 0 || cfg.kernel == 2 || cfg.kernel == 4;
+    const int cb = cfg.kernel == 4 ? 2 : 4;
     if (cfg.ctas == 0)
-        cfg.ctas = ((cfg.kernel == 0 || cfg.kernel == 2) &&
-                    plan_stages(h->stats, (int)val_size(vt), smem_budget(h, 2), cfg.stages, plan)) ? 2 : 1;
-    if (cfg.kernel == 0 || cfg.kernel == 2) {
-        if (!plan_stages(h->stats, (int)val_size(vt), smem_budget(h, cfg.ctas), cfg.stages, plan)) {
-            if (h->kernel_forced && vt == (int)h->dtype)
+        cfg.ctas = (staged && plan_stages(h->stats, (int)val_size(vt), smem_budget(h, 2), cfg.stages, cb, plan)) ? 2 : 1;
+    if (staged) {
+        if (!plan_stages(h->stats, (int)val_size(vt), smem_budget(h, cfg.ctas), cfg.stages, cb, plan)) {
+            if (forced)
                 return fail(CSRK_ERR_UNSUPPORTED, "super-super-rows too large for two shared-memory stages; "
                                                   "choose smaller sizes or the direct kernel");
-            cfg.kernel += 1;   // the SSRs do not fit: fall back to direct loads
+            cfg.kernel = cfg.kernel == 2 ? 3 : 1;   // the SSRs do not fit: fall back to direct loads
         }
     }
     return CSRK_OK;
@@ -311,8 +344,11 @@ int compute(csrk_matrix* h, int32_t k, bool spmm, double alpha, const void* X, i
     KernelConfig cfg;
     StagePlan plan;
     if ((rc = resolve_config(h, vt, cfg, plan))) return rc;
-    if (spmm && cfg.kernel >= 2) cfg.kernel -= 2;   // the pair path is SpMV only
-    if (cfg.kernel >= 2) {
+    // the pair and 16-bit-offset paths are SpMV only
+    if (spmm && (cfg.kernel == 2 || cfg.kernel == 3)) cfg.kernel -= 2;
+    if (spmm && cfg.kernel == 4) cfg.kernel = 0;
+    const bool pairs = cfg.kernel == 2 || cfg.kernel == 3;
+    if (pairs) {
         if ((rc = ensure_vals(h, VAL_DS)) || (rc = ensure_scratch(h, 4, (size_t)n * 8)) ||
             (rc = ensure_scratch(h, 5, 16)))
             return rc;
@@ -340,7 +376,7 @@ int compute(csrk_matrix* h, int32_t k, bool spmm, double alpha, const void* X, i
         const size_t b = (size_t)n * k * esz;
         if ((rc = ensure_scratch(h, 0, b))) return rc;
         if (!fuse_y && (rc = ensure_scratch(h, 1, b))) return rc;
-        if (cfg.kernel < 2) {
+        if (!pairs) {
             int e = launch_gather_rows(xin, ldxin, h->d_scratch[0], k, h->d_perm, n, k, (int)esz, s);
             if (e) return cuda_fail((cudaError_t)e, "permute x");
         }
@@ -356,7 +392,7 @@ int compute(csrk_matrix* h, int32_t k, bool spmm, double alpha, const void* X, i
         }
     }
     const void* xkern = xk;
-    if (cfg.kernel >= 2) {   // permute (when needed) and split x in one pass
+    if (pairs) {   // permute (when needed) and split x in one pass
         const bool gather = !permuted && !x_only;
         int e = launch_split_pairs(static_cast<const double*>(xin), gather ? h->d_perm : nullptr, n,
                                    gather ? static_cast<double*>(h->d_scratch[0]) : nullptr,
@@ -368,8 +404,8 @@ int compute(csrk_matrix* h, int32_t k, bool spmm, double alpha, const void* X, i
     a.desc = h->d_desc;
     a.sr_ptr = h->d_sr_ptr;
     a.rowptr = h->d_rowptr;
-    a.colidx = h->d_colidx;
-    a.vals = h->d_vals[cfg.kernel >= 2 ? (int)VAL_DS : vt];
+    a.colidx = cfg.kernel == 4 ? (const void*)h->d_col16 : (const void*)h->d_colidx;
+    a.vals = h->d_vals[pairs ? (int)VAL_DS : vt];
     a.x = xkern;
     a.x64 = static_cast<const double*>(xk);
     a.xflag = static_cast<const int32_t*>(h->d_scratch[5]);
@@ -412,7 +448,8 @@ int launch_spmv_dev(csrk_matrix* h, int vt, const void* x, void* y, double alpha
     int rc;
     if ((rc = resolve_config(h, vt, cfg, plan))) return rc;
     const void* xkern = x;
-    if (cfg.kernel >= 2) {
+    const bool pairs = cfg.kernel == 2 || cfg.kernel == 3;
+    if (pairs) {
         if ((rc = ensure_vals(h, VAL_DS)) || (rc = ensure_scratch(h, 4, (size_t)h->m.n * 8)) ||
             (rc = ensure_scratch(h, 5, 16)))
             return rc;
@@ -425,8 +462,8 @@ int launch_spmv_dev(csrk_matrix* h, int vt, const void* x, void* y, double alpha
     a.desc = h->d_desc;
     a.sr_ptr = h->d_sr_ptr;
     a.rowptr = h->d_rowptr;
-    a.colidx = h->d_colidx;
-    a.vals = h->d_vals[cfg.kernel >= 2 ? (int)VAL_DS : vt];
+    a.colidx = cfg.kernel == 4 ? (const void*)h->d_col16 : (const void*)h->d_colidx;
+    a.vals = h->d_vals[pairs ? (int)VAL_DS : vt];
     a.x = xkern;
     a.x64 = static_cast<const double*>(x);
     a.xflag = static_cast<const int32_t*>(h->d_scratch[5]);
@@ -607,14 +644,16 @@ int autotune(csrk_matrix* h) {
     else if (rdens <= 64) pairs = {{2, 8}, {2, 16}, {4, 8}};
     else pairs = {{4, 8}, {8, 8}, {32, 4}};
     const bool with_pairs = pairs_available(h);
+    std::vector<TunedChoice> phase2;
     for (size_t b = 0; b < std::min<size_t>(3, phase1.size()) && rc == CSRK_OK; ++b) {
         if ((rc = install(phase1[b].sr, phase1[b].ssr)) || (rc = ensure_struct(h))) break;
         for (auto& pr : pairs)
             for (int warps : {8, 16})
-                for (int kernel : {0, 1, 2, 3})
+                for (int kernel : {0, 1, 2, 3, 4})
                     for (int ctas : {1, 2}) {
                         if ((kernel == 1 || kernel == 3) && ctas == 2) continue;
-                        if (kernel >= 2 && (!with_pairs || pr.first != 1 || pr.second > 16)) continue;
+                        if ((kernel == 2 || kernel == 3) && (!with_pairs || pr.first != 1 || pr.second > 16)) continue;
+                        if (kernel == 4 && (!col16_available(h) || !mode3_compiled(pr.first, pr.second))) continue;
                         KernelConfig c;
                         c.kernel = kernel;
                         c.lanes = pr.first;
@@ -626,13 +665,32 @@ int autotune(csrk_matrix* h) {
                         h->cfg_set = true;
                         h->kernel_forced = (kernel != 1);
                         const float us = time_launches(h, s, e0, e1, reps);
-                        if (us < best.us) {
-                            best.sr = phase1[b].sr;
-                            best.ssr = phase1[b].ssr;
-                            best.cfg = c;
-                            best.us = us;
-                        }
+                        TunedChoice t;
+                        t.sr = phase1[b].sr;
+                        t.ssr = phase1[b].ssr;
+                        t.cfg = c;
+                        t.us = us;
+                        phase2.push_back(t);
                     }
+    }
+    // phase 3: the four fastest shapes (and the best default-shape size pair) re-timed with
+    // longer runs in two interleaved rounds, so that a lucky short timing does not decide
+    if (rc == CSRK_OK) {
+        std::sort(phase2.begin(), phase2.end(), [](auto& a, auto& b) { return a.us < b.us; });
+        std::vector<TunedChoice> finalists(phase2.begin(), phase2.begin() + std::min<size_t>(4, phase2.size()));
+        if (!phase1.empty()) finalists.push_back(phase1.front());   // its resolved default shape
+        for (auto& f : finalists) f.us = 1e30f;
+        for (int round = 0; round < 2 && rc == CSRK_OK; ++round)
+            for (auto& f : finalists) {
+                if ((rc = install(f.sr, f.ssr)) || (rc = ensure_struct(h))) break;
+                h->cfg = f.cfg;
+                h->cfg_set = true;
+                h->kernel_forced = (f.cfg.kernel != 1);
+                f.us = std::min(f.us, time_launches(h, s, e0, e1, 4 * reps));
+            }
+        if (!finalists.empty())
+            best = *std::min_element(finalists.begin(), finalists.end(),
+                                     [](auto& a, auto& b) { return a.us < b.us; });
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -748,6 +806,9 @@ int install_pointers_impl(csrk_handle h, std::vector<int32_t>&& srp, std::vector
     build_descs(h->m, h->sr_ptr, h->ssr_ptr, h->desc, h->stats);
     h->have_ptrs = true;
     if (h->dev_ptrs) free_ptrs(h);   // pointer arrays changed: re-upload on next use
+    cudaFree(h->d_col16);            // the column bases moved with the SSRs
+    h->d_col16 = nullptr;
+    h->col16_ok = -1;
     h->generation++;
     return CSRK_OK;
 }
@@ -776,6 +837,15 @@ int csrk_set_sizes(csrk_handle h, int32_t sr, int32_t ssr) {
     h->sr = sr;
     h->ssr = ssr;
     h->bandk_sr = h->bandk_ssr = 0;
+    return CSRK_OK;
+}
+
+int csrk_index_bits(csrk_handle h, int32_t* bits) {
+    if (!h || !bits) return fail(CSRK_ERR_ARG, "NULL argument");
+    if (!h->have_ptrs) return fail(CSRK_ERR_STATE, "call csrk_set_sizes or csrk_set_pointers first");
+    std::vector<uint16_t> tmp;   // host only: the coding is checked, not uploaded
+    if (h->col16_ok >= 0) *bits = h->col16_ok == 1 ? 16 : 32;
+    else *bits = compress_columns(h->m, h->desc, tmp) ? 16 : 32;
     return CSRK_OK;
 }
 
@@ -923,7 +993,7 @@ int csrk_tuned_config(csrk_handle h, int32_t* kernel, int32_t* lanes, int32_t* u
         KernelConfig r;
         if (resolve_config(h, (int)h->dtype, r, plan) == CSRK_OK) {
             c = r;
-            c.stages = c.kernel == 0 ? plan.stages : 0;
+            c.stages = (c.kernel == 0 || c.kernel == 2 || c.kernel == 4) ? plan.stages : 0;
         }
     }
     if (kernel) *kernel = c.kernel;
@@ -940,7 +1010,7 @@ int csrk_set_config(csrk_handle h, int32_t kernel, int32_t lanes, int32_t unroll
     if (!h) return fail(CSRK_ERR_ARG, "handle is NULL");
     KernelConfig c = h->cfg_set ? h->cfg : default_config(h);
     if (kernel >= 0) {
-        if (kernel > 3) return fail(CSRK_ERR_ARG, "kernel must be 0, 1, 2 or 3");
+        if (kernel > 4) return fail(CSRK_ERR_ARG, "kernel must be 0, 1, 2, 3 or 4");
         c.kernel = kernel;
         h->kernel_forced = (kernel != 1);
     }
@@ -952,7 +1022,7 @@ int csrk_set_config(csrk_handle h, int32_t kernel, int32_t lanes, int32_t unroll
     }
     if (unroll >= 0) c.unroll = unroll;
     if (c.kernel >= 2 && (c.lanes != 1 || (c.unroll != 4 && c.unroll != 8 && c.unroll != 16)))
-        return fail(CSRK_ERR_ARG, "kernels 2 and 3 take lanes 1 and unroll 4, 8 or 16");
+        return fail(CSRK_ERR_ARG, "kernels 2, 3 and 4 take lanes 1 and unroll 4, 8 or 16");
     if (!pair_compiled(c.lanes, c.unroll))
         return fail(CSRK_ERR_ARG, "unsupported (lanes, unroll) pair; compiled: (1,4) (1,8) (1,16) "
                                   "(1,32) (2,8) (2,16) (4,8) (8,8) (32,4)");

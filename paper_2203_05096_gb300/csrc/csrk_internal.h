@@ -25,7 +25,8 @@ struct alignas(16) SsrDesc {
     int32_t s0, s1;   // super-rows [s0, s1)
     int32_t r0, r1;   // rows [r0, r1)
     int32_t p0, p1;   // nonzeros [p0, p1)
-    int32_t pad0, pad1;
+    int32_t cbase;    // smallest column of the SSR (base of its 16-bit column coding)
+    int32_t pad1;
 };
 
 struct TileStats {
@@ -52,6 +53,9 @@ void fixed_pointers(int32_t n, int32_t sr, int32_t ssr, std::vector<int32_t>& sr
                     std::vector<int32_t>& ssr_ptr);
 bool check_pointers(int32_t n, const std::vector<int32_t>& sr_ptr,
                     const std::vector<int32_t>& ssr_ptr, std::string& err);
+// Delta-coded 16-bit columns (first entry of a row from the SSR's cbase, then steps);
+// false when some code exceeds 65,535.
+bool compress_columns(const CsrHost& b, const std::vector<SsrDesc>& desc, std::vector<uint16_t>& col16);
 void build_descs(const CsrHost& b, const std::vector<int32_t>& sr_ptr,
                  const std::vector<int32_t>& ssr_ptr, std::vector<SsrDesc>& desc,
                  TileStats& st);
@@ -69,7 +73,9 @@ enum ValType { VAL_F64 = 0, VAL_F32 = 1, VAL_BF16 = 2, VAL_DS = 3 };
 
 struct KernelConfig {
     int kernel = 0;    // 0 TMA-staged, 1 direct loads; 2 / 3 the same with FP64 values as
-                       // FP32 pairs and FP32-pipe arithmetic (FP64 handles only)
+                       // FP32 pairs and FP32-pipe arithmetic (FP64 handles only); 4 TMA-staged
+                       // with delta-coded 16-bit columns (SpMV, one row per lane, when every
+                       // code fits)
     int lanes = 1;     // lanes per row (SpMV)
     int unroll = 8;    // x gathers issued per lane before the FMAs consume them
     int warps = 8;     // consumer warps per CTA
@@ -82,7 +88,7 @@ struct LaunchArgs {
     const SsrDesc* desc;
     const int32_t* sr_ptr;
     const int32_t* rowptr;
-    const int32_t* colidx;
+    const void* colidx;   // int32 columns, or uint16 offsets when col16
     const void* vals;
     const void* x;
     void* y;
@@ -109,7 +115,7 @@ struct StagePlan {
     uint32_t off_srp, off_rp, off_col, off_val, stage_bytes, header_bytes;
     int stages;
 };
-bool plan_stages(const TileStats& st, int val_bytes, int max_smem, int want_stages,
+bool plan_stages(const TileStats& st, int val_bytes, int max_smem, int want_stages, int col_bytes,
                  StagePlan& plan);
 
 // spmv_*.cu: launch on `stream`; returns a cudaError_t value (0 = success) or -1 when the

@@ -332,6 +332,10 @@ void build_descs(const CsrHost& b, const std::vector<int32_t>& sr_ptr,
         d.r1 = sr_ptr[d.s1];
         d.p0 = b.rowptr[d.r0];
         d.p1 = b.rowptr[d.r1];
+        int32_t lo = 0;
+        for (int64_t p = d.p0; p < d.p1; ++p)
+            if (p == d.p0 || b.colidx[p] < lo) lo = b.colidx[p];
+        d.cbase = lo;
         desc[t] = d;
         st.max_srs = std::max(st.max_srs, d.s1 - d.s0);
         st.max_rows = std::max(st.max_rows, d.r1 - d.r0);
@@ -341,6 +345,26 @@ void build_descs(const CsrHost& b, const std::vector<int32_t>& sr_ptr,
         st.max_sr_rows = std::max(st.max_sr_rows, sr_ptr[s + 1] - sr_ptr[s]);
     for (int32_t i = 0; i < b.n; ++i)
         st.max_row_len = std::max(st.max_row_len, b.rowptr[i + 1] - b.rowptr[i]);
+}
+
+// Delta-coded 16-bit columns: a row's first entry holds its column minus the SSR's
+// cbase, every further entry the step from the previous column (columns ascend within a
+// row).  Exact when every code is at most 65,535; returns false and leaves col16 empty
+// otherwise.
+bool compress_columns(const CsrHost& b, const std::vector<SsrDesc>& desc, std::vector<uint16_t>& col16) {
+    col16.assign(b.colidx.size(), 0);
+    for (const SsrDesc& d : desc)
+        for (int32_t r = d.r0; r < d.r1; ++r)
+            for (int64_t p = b.rowptr[r]; p < b.rowptr[r + 1]; ++p) {
+                const int64_t code = p == b.rowptr[r] ? (int64_t)b.colidx[p] - d.cbase
+                                                      : (int64_t)b.colidx[p] - b.colidx[p - 1];
+                if (code < 0 || code > 65535) {
+                    col16.clear();
+                    return false;
+                }
+                col16[p] = (uint16_t)code;
+            }
+    return true;
 }
 
 // ---------------------------------------------------------------- narrowing

@@ -236,9 +236,13 @@ __device__ __forceinline__ void store_y(XT* y, int64_t idx, AT acc, double alpha
 // chunk's U FMAs in stored order.  Full chunks carry no predicates; the last fewer-than-U
 // entries go in predicated chunks of 4, so a row issues at most 3 idle FP64 slots (wider
 // tail chunks measured slower on the 27-point stencil, where FP64 issue binds).
-template <typename VT, typename XT, typename AT, int LPR, int U>
+// CT is the stored column type: int32_t, or delta-coded uint16_t (one row per lane only):
+// a row's first entry is its column minus the SSR's cbase (folded into x by the caller),
+// every further entry the step from the previous column, so the lane rebuilds the column
+// with one integer add per nonzero.
+template <typename VT, typename XT, typename AT, int LPR, int U, typename CT = int32_t>
 __device__ __forceinline__ void spmv_rows(int rb, int re, const int32_t* __restrict__ rp,
-                                          const int32_t* __restrict__ col_s,
+                                          const CT* __restrict__ col_s,
                                           const VT* __restrict__ val_s,
                                           const XT* __restrict__ x, XT* __restrict__ y,
                                           double alpha, double beta, int epi, int lane,
@@ -249,7 +253,36 @@ __device__ __forceinline__ void spmv_rows(int rb, int re, const int32_t* __restr
     for (int base = rb; base < re; base += RPP) {
         const int r = base + lane / LPR;
         AT acc = 0;
-        if (r < re) {
+        if constexpr (sizeof(CT) == 2) {
+            static_assert(LPR == 1, "delta-coded columns take one row per lane");
+            if (r < re) {
+                const int pe = rp[r + 1];
+                int c = rp[r];
+                int col = 0;
+                for (; c + (U - 1) < pe; c += U) {
+                    XT xv[U];
+#pragma unroll
+                    for (int t = 0; t < U; ++t) {
+                        col += col_s[c + t];
+                        xv[t] = ldg_x(&x[col]);
+                    }
+#pragma unroll
+                    for (int t = 0; t < U; ++t) acc = Acc<AT>::fma(val_s[c + t], xv[t], acc);
+                }
+                for (; c < pe; c += T) {
+                    XT xv[T];
+#pragma unroll
+                    for (int t = 0; t < T; ++t)
+                        if (c + t < pe) {
+                            col += col_s[c + t];
+                            xv[t] = ldg_x(&x[col]);
+                        }
+#pragma unroll
+                    for (int t = 0; t < T; ++t)
+                        if (c + t < pe) acc = Acc<AT>::fma(val_s[c + t], xv[t], acc);
+                }
+            }
+        } else if (r < re) {
             const int pe = rp[r + 1];
             int c = rp[r] + sub;
             for (; c + (U - 1) * LPR < pe; c += U * LPR) {
@@ -404,7 +437,7 @@ struct TmaParams {
     const SsrDesc* desc;
     const int32_t* sr_ptr;
     const int32_t* rowptr;
-    const int32_t* colidx;
+    const void* colidx;    // int32 columns; MODE 3: uint16 offsets from each SSR's cbase
     const void* vals;
     const void* x;
     void* y;
@@ -434,7 +467,9 @@ __device__ __forceinline__ void slice16(int64_t first, int64_t last_excl, int64_
 
 // MODE 0: SpMV with LPR lanes per row and gather chunks of U.  MODE 1: SpMM with G = LPR
 // lanes per row and U columns per lane.  MODE 2: SpMV with FP64 values as FP32 pairs
-// (VT = ds_t, one row per lane, FP64 accuracy on the FP32 pipes).
+// (VT = ds_t, one row per lane, FP64 accuracy on the FP32 pipes).  MODE 3: MODE 0 with
+// delta-coded 16-bit columns (2 bytes per nonzero instead of 4; see spmv_rows), one row
+// per lane, the consumers indexing x + cbase.
 // At most 60 registers per thread, so two blocks of 16 consumer warps + 1 producer warp
 // fit on one SM (65,536 registers).
 template <typename VT, typename XT, typename AT, int LPR, int MODE, int U>
@@ -474,15 +509,18 @@ __global__ void __launch_bounds__(544, 2) csr3_tma_kernel(const TmaParams P) {
                 int64_t a0;
                 uint32_t b_srp, b_rp, b_col, b_val;
                 int64_t o_srp, o_rp, o_col, o_val;
+                constexpr int CSZ = MODE == 3 ? 2 : 4;   // bytes per stored column
                 slice16<4>(d.s0, (int64_t)d.s1 + 1, o_srp, b_srp);
                 slice16<4>(d.r0, (int64_t)d.r1 + 1, o_rp, b_rp);
-                slice16<4>(d.p0, d.p1, o_col, b_col);
+                slice16<CSZ>(d.p0, d.p1, o_col, b_col);
                 slice16<sizeof(VT)>(d.p0, d.p1, o_val, b_val);
                 (void)a0;
                 mbar_arrive_expect_tx(&full[s], b_srp + b_rp + b_col + b_val);
                 bulk_g2s(st + P.off_srp, P.sr_ptr + o_srp, b_srp, &full[s], pol);
                 bulk_g2s(st + P.off_rp, P.rowptr + o_rp, b_rp, &full[s], pol);
-                if (b_col) bulk_g2s(st + P.off_col, P.colidx + o_col, b_col, &full[s], pol);
+                if (b_col)
+                    bulk_g2s(st + P.off_col, static_cast<const unsigned char*>(P.colidx) + o_col * CSZ, b_col,
+                             &full[s], pol);
                 if (b_val)
                     bulk_g2s(st + P.off_val, static_cast<const VT*>(P.vals) + o_val, b_val,
                              &full[s], pol);
@@ -511,6 +549,8 @@ __global__ void __launch_bounds__(544, 2) csr3_tma_kernel(const TmaParams P) {
         const int32_t* srp = reinterpret_cast<const int32_t*>(st + P.off_srp) - (d.s0 & ~3);
         const int32_t* rp = reinterpret_cast<const int32_t*>(st + P.off_rp) - (d.r0 & ~3);
         const int32_t* col = reinterpret_cast<const int32_t*>(st + P.off_col) - (d.p0 & ~3);
+        const uint16_t* col16 = reinterpret_cast<const uint16_t*>(st + P.off_col) - (d.p0 & ~7);
+        (void)col16;
         constexpr int VPER = 16 / (int)sizeof(VT);
         const VT* val = reinterpret_cast<const VT*>(st + P.off_val) - (d.p0 & ~(VPER - 1));
         const int nsr = d.s1 - d.s0;
@@ -525,6 +565,9 @@ __global__ void __launch_bounds__(544, 2) csr3_tma_kernel(const TmaParams P) {
             else if constexpr (MODE == 0)
                 spmv_rows<VT, XT, AT, LPR, U>(rb, re, rp, col, val, x, y, P.alpha, P.beta, P.epi,
                                               lane, P.yperm);
+            else if constexpr (MODE == 3)
+                spmv_rows<VT, XT, AT, LPR, U, uint16_t>(rb, re, rp, col16, val, x + d.cbase, y, P.alpha,
+                                                        P.beta, P.epi, lane, P.yperm);
             else
                 spmm_rows<VT, XT, AT, LPR, U>(rb, re, rp, col, val, x, P.ldx, y, P.ldy, P.k,
                                                P.alpha, P.beta, P.epi, lane);
@@ -553,14 +596,15 @@ __global__ void __launch_bounds__(512, 1) csr3_direct_kernel(const TmaParams P) 
         const SsrDesc d = P.desc[t];
         for (int sr = d.s0 + warp; sr < d.s1; sr += W) {
             const int rb = __ldg(&P.sr_ptr[sr]), re = __ldg(&P.sr_ptr[sr + 1]);
+            const int32_t* cols = static_cast<const int32_t*>(P.colidx);
             if constexpr (MODE == 2)
-                spmv_rows_ds<U>(rb, re, P.rowptr, P.colidx, vals, reinterpret_cast<const xpair*>(P.x),
+                spmv_rows_ds<U>(rb, re, P.rowptr, cols, vals, reinterpret_cast<const xpair*>(P.x),
                                 P.x64, slow, y, P.alpha, P.beta, P.epi, lane, P.yperm);
             else if constexpr (MODE == 0)
-                spmv_rows<VT, XT, AT, LPR, U>(rb, re, P.rowptr, P.colidx, vals, x, y, P.alpha,
+                spmv_rows<VT, XT, AT, LPR, U>(rb, re, P.rowptr, cols, vals, x, y, P.alpha,
                                               P.beta, P.epi, lane, P.yperm);
             else
-                spmm_rows<VT, XT, AT, LPR, U>(rb, re, P.rowptr, P.colidx, vals, x, P.ldx, y,
+                spmm_rows<VT, XT, AT, LPR, U>(rb, re, P.rowptr, cols, vals, x, P.ldx, y,
                                                P.ldy, P.k, P.alpha, P.beta, P.epi, lane);
         }
     }

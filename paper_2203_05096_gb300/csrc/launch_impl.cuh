@@ -59,11 +59,13 @@ static int launch_one(const LaunchArgs& a, const KernelConfig& cfg, const StageP
         int grid = a.num_sms * cfg.ctas;
         if (grid > a.nssr) grid = a.nssr;
         kern<<<grid, threads, smem, stream>>>(P);
-    } else {
+    } else if constexpr (MODE != 3) {   // 16-bit offsets are staged only
         auto kern = csr3_direct_kernel<VT, XT, AT, LPR, MODE, U>;
         const int threads = 32 * cfg.warps;
         int grid = a.nssr;
         kern<<<grid, threads, 0, stream>>>(P);
+    } else {
+        return -1;
     }
     return (int)cudaGetLastError();
 }
@@ -76,6 +78,17 @@ static int launch_one(const LaunchArgs& a, const KernelConfig& cfg, const StageP
 template <typename VT, typename XT, typename AT>
 static int dispatch_lanes(const LaunchArgs& a, const KernelConfig& cfg, const StagePlan& plan,
                           cudaStream_t s) {
+    if (cfg.kernel == 4) {   // 16-bit column offsets: TMA-staged SpMV, one row per lane
+        if (a.spmm || cfg.lanes != 1) return -1;
+        KernelConfig c = cfg;
+        c.kernel = 0;
+        switch (cfg.unroll) {
+            case 4: return launch_one<VT, XT, AT, 1, 3, 4>(a, c, plan, s);
+            case 8: return launch_one<VT, XT, AT, 1, 3, 8>(a, c, plan, s);
+            case 16: return launch_one<VT, XT, AT, 1, 3, 16>(a, c, plan, s);
+            default: return -1;
+        }
+    }
     if (!a.spmm) {
         CSRK_SPMV_CASE(1, 4)
         CSRK_SPMV_CASE(1, 8)

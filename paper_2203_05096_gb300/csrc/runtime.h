@@ -39,6 +39,8 @@ struct csrk_matrix {
     bool dev_ptrs = false;         // sr_ptr/desc uploaded
     int32_t* d_rowptr = nullptr;
     int32_t* d_colidx = nullptr;
+    uint16_t* d_col16 = nullptr;   // 16-bit column offsets from each SSR's cbase (kernel 4)
+    int col16_ok = -1;             // offsets usable with the current pointers; -1 unknown
     void* d_vals[4] = {nullptr, nullptr, nullptr, nullptr};   // by ValType
     int pairs_ok = -1;             // FP32-pair path usable (values in range); -1 unknown
     int32_t* d_sr_ptr = nullptr;
@@ -68,6 +70,8 @@ int ensure_vals(csrk_matrix* h, int vt);
 int ensure_scratch(csrk_matrix* h, int slot, size_t bytes);
 KernelConfig default_config(const csrk_matrix* h);
 bool pairs_available(csrk_matrix* h);
+bool col16_available(csrk_matrix* h);
+bool mode3_compiled(int lanes, int unroll);
 int resolve_config(csrk_matrix* h, int vt, KernelConfig& cfg, StagePlan& plan);
 int compute(csrk_matrix* h, int32_t k, bool spmm, double alpha, const void* X, int64_t ldx,
             double beta, void* Y, int64_t ldy, unsigned flags, void* stream);

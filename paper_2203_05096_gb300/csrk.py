@@ -44,6 +44,7 @@ _PROTOS = {
     "csrk_create": [_i32, _vp, _vp, _vp, ctypes.c_int, ctypes.POINTER(_vp)],
     "csrk_reorder": [_vp, ctypes.c_int, _vp],
     "csrk_reorder_bandk": [_vp, _i32, _i32, _vp],
+    "csrk_index_bits": [_vp, _pi32],
     "csrk_set_sizes": [_vp, _i32, _i32],
     "csrk_set_pointers": [_vp, _i32, _vp, _i32, _vp],
     "csrk_spmv": [_vp, _d, _vp, _d, _vp, _u, _vp],
@@ -158,6 +159,12 @@ def reorder_bandk(h, sr, ssr, want_perm=True):
 
 def set_sizes(h, sr, ssr):
     _check(lib().csrk_set_sizes(h, int(sr), int(ssr)), "csrk_set_sizes")
+
+
+def index_bits(h):
+    v = ctypes.c_int32()
+    _check(lib().csrk_index_bits(h, ctypes.byref(v)), "csrk_index_bits")
+    return v.value
 
 
 def set_pointers(h, sr_ptr, ssr_ptr):

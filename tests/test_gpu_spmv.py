@@ -462,3 +462,57 @@ def test_bandk_autotune_keeps_pointers():
     assert np.array_equal(csrk.export(h)["perm"], before["perm"]) and csrk.info(h)["sr"] == 32
     assert_close(gpu_spmv(h, x), a, a.vals, x)
     csrk.destroy(h)
+
+
+# ------------------------------------------------------------------ 16-bit column offsets
+@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16"])
+@pytest.mark.parametrize("unroll", [4, 8, 16])
+def test_col16_kernel_bit_exact_with_kernel0(dtype, unroll):
+    """Kernel 4 reads 16-bit column offsets from each SSR's smallest column; the products
+    and their order are kernel 0's, so the results are bit-identical."""
+    a = small_27pt(23)
+    x = synth.uniform_vector(a.n, 41)
+    y0 = synth.uniform_vector(a.n, 42)
+    h = make(a, 32, 4, dtype=dtype)
+    assert csrk.index_bits(h) == 16
+    out = {}
+    for kernel in (0, 4):
+        csrk.set_config(h, kernel=kernel, lanes=1, unroll=unroll, warps=16)
+        out[kernel] = (gpu_spmv(h, x, 1.25, 0.5, y0), gpu_spmv(h, x))
+    assert np.array_equal(out[0][0], out[4][0]) and np.array_equal(out[0][1], out[4][1])
+    if dtype == "f64":
+        assert_close(out[4][0], a, a.vals, x, 1.25, 0.5, y0)
+    csrk.destroy(h)
+
+
+def test_col16_full_size_27pt_fused_unpermute():
+    a = _full_stencil(27)
+    h = make(a, 32, 2)
+    assert csrk.index_bits(h) == 16
+    csrk.set_config(h, kernel=4, lanes=1, unroll=16, warps=16, ctas=2)
+    x = synth.uniform_vector(a.n, 43)
+    got = gpu_spmv(h, x)
+    rows = np.random.default_rng(7).integers(0, a.n, 4000)
+    ref = ospmv.csr_spmv_rows(a.rowptr, a.colidx, a.vals, x, rows)
+    s = ospmv.abs_row_scale(a.rowptr, a.colidx, a.vals, x, rows=rows)
+    assert np.all(np.abs(got[rows] - ref) <= 1e-12 * s)
+    csrk.set_config(h, kernel=0)
+    assert np.array_equal(gpu_spmv(h, x), got)
+    csrk.destroy(h)
+
+
+def test_col16_refused_when_the_span_is_too_wide():
+    a = synth.stencil_3d(50, 50, 50, 7, "random_dd", 4, labels=synth.vectors.permutation(125000, 4))
+    h = csrk.create(a.n, a.rowptr, a.colidx, a.vals)
+    csrk.set_sizes(h, 32, 8)                          # no reordering: spans of ~125K columns
+    assert csrk.index_bits(h) == 32
+    csrk.set_config(h, kernel=4, lanes=1, unroll=8)
+    x = torch.tensor(synth.uniform_vector(a.n, 44), device=DEV)
+    with pytest.raises(csrk.CsrkError) as ei:
+        csrk.spmv(h, 1.0, x, 0.0, torch.empty_like(x))
+    assert ei.value.status == "ERR_UNSUPPORTED"
+    csrk.set_sizes(h, 0, 0)                           # the autotuner never picks it here
+    assert csrk.tuned_config(h)["kernel"] != 4
+    got = gpu_spmv(h, x.cpu().numpy())
+    assert_close(got, a, a.vals, x.cpu().numpy())
+    csrk.destroy(h)

@@ -169,3 +169,34 @@ def test_bandk_large_stencil_invariants():
     # most super-rows are full: the aggregates pack the grid
     assert np.mean(np.diff(e["sr_ptr"])) > 24
     csrk.destroy(h)
+
+
+# ------------------------------------------------------------------ 16-bit column offsets
+def test_index_bits_follow_the_ssr_column_span():
+    a = synth.stencil_3d(40, 40, 40, 27, "random_dd", 4, labels=synth.vectors.permutation(64000, 4))
+    h = csrk.create(a.n, a.rowptr, a.colidx, a.vals)
+    with pytest.raises(csrk.CsrkError) as ei:
+        csrk.index_bits(h)
+    assert ei.value.status == "ERR_STATE"
+    csrk.reorder(h)
+    csrk.set_sizes(h, 32, 8)
+    assert csrk.index_bits(h) == 16                  # RCM: steps within a row of ~1.7K at most
+    csrk.destroy(h)
+    # without reordering, random labels put steps of up to ~125K columns inside rows
+    a = synth.stencil_3d(50, 50, 50, 7, "random_dd", 4, labels=synth.vectors.permutation(125000, 4))
+    h = csrk.create(a.n, a.rowptr, a.colidx, a.vals)
+    csrk.set_sizes(h, 32, 8)
+    assert csrk.index_bits(h) == 32
+    csrk.destroy(h)
+    # a step of 65,535 between two columns of a row fits, 65,536 does not
+    for far, bits in [(65535, 16), (65536, 32)]:
+        n = 70000
+        rows = [[i] for i in range(n)]
+        rows[0].append(far)
+        rows[far].append(0)
+        rp = np.array([0] + list(np.cumsum([len(r) for r in rows])), np.int32)
+        ci = np.array([c for r in rows for c in sorted(r)], np.int32)
+        h = csrk.create(n, rp, ci, np.ones(ci.size))
+        csrk.set_sizes(h, 32, 8)
+        assert csrk.index_bits(h) == bits, far
+        csrk.destroy(h)
