@@ -48,10 +48,13 @@ SR, SSR = 32, 8
 MATRICES = (("stencil7", 7), ("stencil27", 27))
 
 # DRAM traffic per launch of the dominant kernel from an ncu capture, keyed by (matrix,
-# dtype, kernel number) and valid only for the kernel source it was taken on.  The 27-point entry is the 96^3 capture summarised in
-# profiles/csr3_tma_27pt_96cubed_f64.md (299.20 MB) scaled to 128^3 by nonzeros.
+# dtype, kernel number) and valid only for the kernel source it was taken on.  Each entry
+# is a 96^3 capture (profiles/csr3_tma_27pt_96cubed_f64.md: 299.20 MB, kernel 0;
+# profiles/csr3_tma_k4_27pt_96cubed_f64.md: 252.25 MB, kernel 4) scaled to 128^3 by
+# nonzeros.
 NCU_TRAFFIC = {
     ("stencil27", "f64", 0): {"bytes": 712_940_980, "kernel_hash": "871b5d682a86"},
+    ("stencil27", "f64", 4): {"bytes": 601_073_144, "kernel_hash": "6685092d4e31"},
 }
 
 
