@@ -133,6 +133,20 @@ int csrk_reorder(csrk_handle h, int method, int32_t* perm_out);
  * Host only. */
 int csrk_reorder_bandk(csrk_handle h, int32_t sr, int32_t ssr, int32_t* perm_out);
 
+/* csrk_split_long_rows: the irregular-matrix path (Sec. 7 names the row mapping of
+ * irregular matrices as future work).  Rows with at least min_len stored entries are moved
+ * behind all other rows (a symmetric renumbering composed with any earlier reorder, each
+ * group keeping its order) and left out of the super-rows: the pointer arrays built
+ * afterwards cover the first n - n_long rows only.  Every SpMV / SpMM / CG launch then
+ * also computes the long rows in segments of 2,048 entries, one warp per segment and
+ * right-hand side, and sums each row's segment partials in segment order (deterministic).
+ *   min_len   threshold, >= 1
+ *   n_long    optional: receives the number of rows moved
+ * Call after csrk_reorder (CSRK_ERR_STATE if the pointer arrays exist; csrk_reorder and
+ * csrk_reorder_bandk refuse a handle with split rows).  Batches refuse such handles.
+ * Host only. */
+int csrk_split_long_rows(csrk_handle h, int32_t min_len, int32_t* n_long);
+
 /* csrk_set_sizes: build sr_ptr / ssr_ptr for fixed sizes (Sec. 2.2): every super-row
  * holds sr rows and every super-super-row ssr super-rows, the last of each possibly
  * fewer.  sr = ssr = 0 asks the autotuner to choose (it times candidates on the GPU,
@@ -150,7 +164,7 @@ int csrk_index_bits(csrk_handle h, int32_t* bits);
 /* csrk_set_pointers: give the super-row and super-super-row pointer arrays explicitly
  * (variable sizes, e.g. Fig. 1: sr_ptr = {0,2,5,7,9}, ssr_ptr = {0,2,4}).
  *   nsr     number of super-rows; sr_ptr has nsr+1 entries, sr_ptr[0] = 0,
- *           sr_ptr[nsr] = n, non-decreasing
+ *           sr_ptr[nsr] = n (n - n_long after csrk_split_long_rows), non-decreasing
  *   nssr    number of super-super-rows; ssr_ptr has nssr+1 entries, ssr_ptr[0] = 0,
  *           ssr_ptr[nssr] = nsr, non-decreasing
  * Errors: CSRK_ERR_ARG for arrays that break these rules.  Host only. */

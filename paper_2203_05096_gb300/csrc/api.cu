@@ -42,8 +42,14 @@ namespace rt {
 void free_ptrs(csrk_matrix* h) {
     cudaFree(h->d_sr_ptr);
     cudaFree(h->d_desc);
+    cudaFree(h->d_lseg);
+    cudaFree(h->d_lseg_ptr);
+    cudaFree(h->d_lpart);
     h->d_sr_ptr = nullptr;
     h->d_desc = nullptr;
+    h->d_lseg = nullptr;
+    h->d_lseg_ptr = nullptr;
+    h->d_lpart = nullptr;
     h->dev_ptrs = false;
 }
 
@@ -126,6 +132,12 @@ int ensure_struct(csrk_matrix* h) {
     if (!h->dev_ptrs) {
         if ((rc = upload_padded(&h->d_sr_ptr, h->sr_ptr.data(), h->sr_ptr.size(), 4, "sr_ptr"))) return rc;
         if ((rc = upload_padded(&h->d_desc, h->desc.data(), h->desc.size(), sizeof(SsrDesc), "desc"))) return rc;
+        if (h->n_long > 0) {
+            if ((rc = upload_padded(&h->d_lseg, h->lseg.data(), h->lseg.size(), sizeof(LongSeg), "long segments")) ||
+                (rc = upload_padded(&h->d_lseg_ptr, h->lseg_ptr.data(), h->lseg_ptr.size(), 4, "long rows")))
+                return rc;
+            CK_CUDA(cudaMalloc(&h->d_lpart, h->lseg.size() * 64 * sizeof(double)), "long-row partials");
+        }
         h->dev_ptrs = true;
     }
     return CSRK_OK;
@@ -261,16 +273,33 @@ bool csrk::plan_stages(const TileStats& st, int val_bytes, int max_smem, int wan
 
 int csrk::launch_csr3(const LaunchArgs& a, const KernelConfig& cfg, const StagePlan& plan,
                       void* stream) {
-    if (cfg.kernel == 2 || cfg.kernel == 3) return launch_csr3_ds(a, cfg, plan, stream);
-    switch (a.val_type) {
-        case VAL_F64: return launch_csr3_f64(a, cfg, plan, stream);
-        case VAL_F32: return launch_csr3_f32(a, cfg, plan, stream);
-        default: return launch_csr3_bf16(a, cfg, plan, stream);
-    }
+    int e;
+    if (cfg.kernel == 2 || cfg.kernel == 3) e = launch_csr3_ds(a, cfg, plan, stream);
+    else if (a.val_type == VAL_F64) e = launch_csr3_f64(a, cfg, plan, stream);
+    else if (a.val_type == VAL_F32) e = launch_csr3_f32(a, cfg, plan, stream);
+    else e = launch_csr3_bf16(a, cfg, plan, stream);
+    if (e == 0 && a.n_long > 0) e = launch_long_rows(a, stream);
+    return e;
 }
 
 namespace csrk {
 namespace rt {
+
+// The long rows of a launch (csrk_split_long_rows): int32 columns, and for the pair path
+// the FP64 values and x.
+void fill_long_rows(const csrk_matrix* h, LaunchArgs& a, bool pairs) {
+    if (h->n_long == 0) return;
+    a.n_long = h->n_long;
+    a.row0_long = h->m.n - h->n_long;
+    a.nlseg = (int32_t)h->lseg.size();
+    a.lseg = h->d_lseg;
+    a.lseg_ptr = h->d_lseg_ptr;
+    a.lpart = h->d_lpart;
+    a.lcolidx = h->d_colidx;
+    a.lvals = pairs ? h->d_vals[VAL_F64] : a.vals;
+    a.lval_type = pairs ? (int)VAL_F64 : a.val_type;
+    a.lx = pairs ? static_cast<const void*>(a.x64) : a.x;
+}
 
 // Resolve the launch configuration and stage plan for this handle and value type.
 int resolve_config(csrk_matrix* h, int vt, KernelConfig& cfg, StagePlan& plan) {
@@ -426,6 +455,7 @@ int compute(csrk_matrix* h, int32_t k, bool spmm, double alpha, const void* X, i
     a.spmm = spmm;
     a.num_sms = h->num_sms;
     a.timeout_ns = h->timeout_ns;
+    fill_long_rows(h, a, pairs);
     int e = launch_csr3(a, cfg, plan, s);
     if (e == -1) return fail(CSRK_ERR_UNSUPPORTED, "kernel variant not compiled for this configuration");
     if (e) return cuda_fail((cudaError_t)e, "CSR-3 kernel launch");
@@ -482,6 +512,7 @@ int launch_spmv_dev(csrk_matrix* h, int vt, const void* x, void* y, double alpha
     a.spmm = false;
     a.num_sms = h->num_sms;
     a.timeout_ns = h->timeout_ns;
+    fill_long_rows(h, a, pairs);
     int e = launch_csr3(a, cfg, plan, s);
     if (e == -1) return fail(CSRK_ERR_UNSUPPORTED, "kernel variant not compiled for this configuration");
     if (e) return cuda_fail((cudaError_t)e, "CSR-3 kernel launch");
@@ -516,7 +547,7 @@ int install_pointers_impl(csrk_handle h, std::vector<int32_t>&& srp, std::vector
 
 int set_fixed(csrk_matrix* h, int32_t sr, int32_t ssr) {
     std::vector<int32_t> srp, ssrp;
-    fixed_pointers(h->m.n, sr, ssr, srp, ssrp);
+    fixed_pointers(h->m.n - h->n_long, sr, ssr, srp, ssrp);
     int rc = install_pointers_impl(h, std::move(srp), std::move(ssrp));
     if (rc) return rc;
     h->sr = sr;
@@ -529,7 +560,8 @@ std::string tune_key(const csrk_matrix* h) {
     cudaGetDeviceProperties(&prop, h->device);
     return std::to_string(h->m.n) + ":" + std::to_string(h->m.nnz()) + ":" +
            std::to_string(h->stats.max_row_len) + ":" + std::to_string((int)h->dtype) + ":" +
-           std::to_string(h->num_sms) + ":" + std::string(prop.name);
+           std::to_string(h->num_sms) + ":" + std::string(prop.name) +
+           (h->n_long ? ":long" + std::to_string(h->n_long) : std::string());
 }
 
 void load_tune_file() {
@@ -740,6 +772,7 @@ int csrk_create(int32_t n, const int32_t* rowptr, const int32_t* colidx, const d
 int csrk_reorder(csrk_handle h, int method, int32_t* perm_out) {
     if (!h) return fail(CSRK_ERR_ARG, "handle is NULL");
     if (h->have_ptrs) return fail(CSRK_ERR_STATE, "reorder must come before csrk_set_sizes / csrk_set_pointers");
+    if (h->n_long > 0) return fail(CSRK_ERR_STATE, "reorder must come before csrk_split_long_rows");
     if (method != CSRK_REORDER_NONE && method != CSRK_REORDER_RCM) return fail(CSRK_ERR_ARG, "unknown method");
     try {
         if (method == CSRK_REORDER_RCM) {
@@ -768,6 +801,7 @@ int csrk_reorder(csrk_handle h, int method, int32_t* perm_out) {
 int csrk_reorder_bandk(csrk_handle h, int32_t sr, int32_t ssr, int32_t* perm_out) {
     if (!h) return fail(CSRK_ERR_ARG, "handle is NULL");
     if (h->have_ptrs) return fail(CSRK_ERR_STATE, "reorder must come before csrk_set_sizes / csrk_set_pointers");
+    if (h->n_long > 0) return fail(CSRK_ERR_STATE, "Band-k does not take split long rows");
     if (sr < 1 || ssr < 1) return fail(CSRK_ERR_ARG, "sr and ssr must be >= 1");
     try {
         std::vector<int32_t> local, srp, ssrp;
@@ -795,15 +829,62 @@ int csrk_reorder_bandk(csrk_handle h, int32_t sr, int32_t ssr, int32_t* perm_out
     return CSRK_OK;
 }
 
+int csrk_split_long_rows(csrk_handle h, int32_t min_len, int32_t* n_long) {
+    if (!h) return fail(CSRK_ERR_ARG, "handle is NULL");
+    if (h->have_ptrs) return fail(CSRK_ERR_STATE, "split long rows before csrk_set_sizes / csrk_set_pointers");
+    if (min_len < 1) return fail(CSRK_ERR_ARG, "min_len must be >= 1");
+    try {
+        const int32_t n = h->m.n;
+        std::vector<int32_t> local;   // short rows in order, then long rows in order
+        local.reserve(n);
+        for (int pass = 0; pass < 2; ++pass)
+            for (int32_t i = 0; i < n; ++i) {
+                const bool is_long = h->m.rowptr[i + 1] - h->m.rowptr[i] >= min_len;
+                if (is_long == (pass == 1)) local.push_back(i);
+            }
+        int32_t count = 0;
+        for (int32_t i = 0; i < n; ++i) count += (h->m.rowptr[i + 1] - h->m.rowptr[i] >= min_len);
+        if (count > 0) {
+            CsrHost b;
+            permute_symmetric(h->m, local, b);
+            h->m = std::move(b);
+            if (!h->perm.empty())
+                for (auto& p : local) p = h->perm[p];
+            h->perm = std::move(local);
+            if (h->device >= 0) {   // the matrix changed: re-upload on next use
+                free_struct(h);
+                for (auto& v : h->d_vals) {
+                    cudaFree(v);
+                    v = nullptr;
+                }
+            }
+            h->pairs_ok = -1;
+        }
+        h->n_long = count;
+        if (n_long) *n_long = count;
+    } catch (const std::bad_alloc&) {
+        return fail(CSRK_ERR_ALLOC, "out of host memory");
+    }
+    return CSRK_OK;
+}
+
 }  // extern "C"
 
 namespace {
 int install_pointers_impl(csrk_handle h, std::vector<int32_t>&& srp, std::vector<int32_t>&& ssrp) {
     std::string err;
-    if (!check_pointers(h->m.n, srp, ssrp, err)) return fail(CSRK_ERR_ARG, err);
+    if (!check_pointers(h->m.n - h->n_long, srp, ssrp, err)) return fail(CSRK_ERR_ARG, err);
     h->sr_ptr = std::move(srp);
     h->ssr_ptr = std::move(ssrp);
     build_descs(h->m, h->sr_ptr, h->ssr_ptr, h->desc, h->stats);
+    // the long rows' segments, row by row
+    h->lseg.clear();
+    h->lseg_ptr.assign(1, 0);
+    for (int32_t r = h->m.n - h->n_long; r < h->m.n; ++r) {
+        for (int64_t p = h->m.rowptr[r]; p < h->m.rowptr[r + 1]; p += LSEG)
+            h->lseg.push_back({(int32_t)p, (int32_t)std::min<int64_t>(p + LSEG, h->m.rowptr[r + 1])});
+        h->lseg_ptr.push_back((int32_t)h->lseg.size());
+    }
     h->have_ptrs = true;
     if (h->dev_ptrs) free_ptrs(h);   // pointer arrays changed: re-upload on next use
     cudaFree(h->d_col16);            // the column bases moved with the SSRs
@@ -828,7 +909,7 @@ int csrk_set_sizes(csrk_handle h, int32_t sr, int32_t ssr) {
     if (sr <= 0 || ssr <= 0) return fail(CSRK_ERR_ARG, "sizes must be positive");
     try {
         std::vector<int32_t> srp, ssrp;
-        fixed_pointers(h->m.n, sr, ssr, srp, ssrp);
+        fixed_pointers(h->m.n - h->n_long, sr, ssr, srp, ssrp);
         int rc = install_pointers_impl(h, std::move(srp), std::move(ssrp));
         if (rc) return rc;
     } catch (const std::bad_alloc&) {

@@ -863,6 +863,7 @@ int csrk_batch_create(const csrk_handle* hs, int32_t count, const int32_t* k, cs
         for (int32_t i = 0; i < count && !rc; ++i) {
             csrk_matrix* h = hs[i];
             if (!h || !h->have_ptrs) { rc = fail(CSRK_ERR_STATE, "every batch matrix needs its pointer arrays"); break; }
+            if (h->n_long > 0) { rc = fail(CSRK_ERR_UNSUPPORTED, "batched matrices take no split long rows"); break; }
             if (k[i] < 1 || k[i] > 64) { rc = fail(CSRK_ERR_ARG, "k must be in [1, 64]"); break; }
             if ((rc = ensure_context(h)) || (rc = ensure_struct(h)) || (rc = ensure_vals(h, (int)h->dtype))) break;
             if (h->device != dev) { rc = fail(CSRK_ERR_STATE, "batch matrices must live on the current device"); break; }

@@ -83,6 +83,12 @@ struct KernelConfig {
     int ctas = 1;      // CTAs per SM
 };
 
+// A segment [p0, p1) of one long row's nonzeros (the irregular-matrix path).
+struct LongSeg {
+    int32_t p0, p1;
+};
+constexpr int32_t LSEG = 2048;   // nonzeros per long-row segment
+
 // Arguments of one SpMV / SpMM launch over the device CSR-k form.
 struct LaunchArgs {
     const SsrDesc* desc;
@@ -108,6 +114,16 @@ struct LaunchArgs {
     bool spmm;
     int num_sms;
     unsigned long long timeout_ns;
+    // rows left out of the super-rows (csrk_split_long_rows): rows row0_long .. +n_long,
+    // computed by launch_long_rows from int32 columns, values of lval_type and x = lx
+    int32_t n_long = 0, row0_long = 0, nlseg = 0;
+    const LongSeg* lseg = nullptr;
+    const int32_t* lseg_ptr = nullptr;
+    void* lpart = nullptr;
+    const int32_t* lcolidx = nullptr;
+    const void* lvals = nullptr;
+    const void* lx = nullptr;
+    int lval_type = 0;
 };
 
 // Shared-memory plan of the TMA kernel for one value type.
@@ -126,6 +142,8 @@ int launch_csr3_f64(const LaunchArgs& a, const KernelConfig& cfg, const StagePla
 int launch_csr3_f32(const LaunchArgs& a, const KernelConfig& cfg, const StagePlan& plan, void* stream);
 int launch_csr3_bf16(const LaunchArgs& a, const KernelConfig& cfg, const StagePlan& plan, void* stream);
 int launch_csr3_ds(const LaunchArgs& a, const KernelConfig& cfg, const StagePlan& plan, void* stream);
+// The long rows of a launch (no-op when a.n_long == 0); long_rows.cu.
+int launch_long_rows(const LaunchArgs& a, void* stream);
 
 // api.cu: message returned by csrk_last_error() for the calling thread.
 void set_last_error(const std::string& msg);

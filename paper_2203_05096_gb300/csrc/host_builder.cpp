@@ -343,7 +343,8 @@ void build_descs(const CsrHost& b, const std::vector<int32_t>& sr_ptr,
     }
     for (size_t s = 0; s + 1 < sr_ptr.size(); ++s)
         st.max_sr_rows = std::max(st.max_sr_rows, sr_ptr[s + 1] - sr_ptr[s]);
-    for (int32_t i = 0; i < b.n; ++i)
+    const int32_t covered = sr_ptr.empty() ? 0 : sr_ptr.back();   // long rows lie beyond
+    for (int32_t i = 0; i < covered; ++i)
         st.max_row_len = std::max(st.max_row_len, b.rowptr[i + 1] - b.rowptr[i]);
 }
 

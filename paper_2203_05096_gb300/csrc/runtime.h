@@ -23,6 +23,12 @@ struct csrk_matrix {
     bool have_ptrs = false;
     int32_t sr = 0, ssr = 0;       // fixed sizes (0 when given explicitly)
     int32_t bandk_sr = 0, bandk_ssr = 0;   // caps of the Band-k pointers in place (0: none)
+    int32_t n_long = 0;            // rows moved behind the super-rows (csrk_split_long_rows)
+    std::vector<csrk::LongSeg> lseg;      // their segments, row by row
+    std::vector<int32_t> lseg_ptr;        // n_long + 1: segments of long row i
+    csrk::LongSeg* d_lseg = nullptr;
+    int32_t* d_lseg_ptr = nullptr;
+    void* d_lpart = nullptr;              // per-segment partial sums (up to 64 columns)
     std::vector<int32_t> sr_ptr, ssr_ptr;
     std::vector<SsrDesc> desc;
     TileStats stats;

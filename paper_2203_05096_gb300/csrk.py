@@ -45,6 +45,7 @@ _PROTOS = {
     "csrk_reorder": [_vp, ctypes.c_int, _vp],
     "csrk_reorder_bandk": [_vp, _i32, _i32, _vp],
     "csrk_index_bits": [_vp, _pi32],
+    "csrk_split_long_rows": [_vp, _i32, _pi32],
     "csrk_set_sizes": [_vp, _i32, _i32],
     "csrk_set_pointers": [_vp, _i32, _vp, _i32, _vp],
     "csrk_spmv": [_vp, _d, _vp, _d, _vp, _u, _vp],
@@ -146,6 +147,13 @@ def reorder(h, method="rcm", want_perm=True):
     _check(lib().csrk_reorder(h, REORDER[method], None if perm is None else perm.ctypes.data_as(_vp)),
            "csrk_reorder")
     return perm
+
+
+def split_long_rows(h, min_len):
+    """Move rows with at least min_len entries behind the super-rows; returns their count."""
+    v = ctypes.c_int32()
+    _check(lib().csrk_split_long_rows(h, int(min_len), ctypes.byref(v)), "csrk_split_long_rows")
+    return v.value
 
 
 def reorder_bandk(h, sr, ssr, want_perm=True):

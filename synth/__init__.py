@@ -10,9 +10,9 @@ SuiteSparse suite (Sec. 5.3, Table 1: N of 1-6 M, row density 2-35, row-length v
 <= 10), which are not available here: finite-difference stencils on structured grids and
 an unstructured finite-element-like point cloud.
 """
-from .matrices import (CSR, stencil_2d_5pt, stencil_3d, fem_like, random_pattern,
+from .matrices import (CSR, stencil_2d_5pt, stencil_3d, fem_like, random_pattern, with_dense_rows,
                        relabel, batch_specs, batch_matrix)
 from .vectors import uniform_vector, uniform_block
 
-__all__ = ["CSR", "stencil_2d_5pt", "stencil_3d", "fem_like", "random_pattern", "relabel",
+__all__ = ["CSR", "stencil_2d_5pt", "stencil_3d", "fem_like", "random_pattern", "with_dense_rows", "relabel",
            "batch_specs", "batch_matrix", "uniform_vector", "uniform_block"]

@@ -218,6 +218,44 @@ def random_pattern(n: int, density: float, seed: int, symmetric: bool = False,
     return out
 
 
+def with_dense_rows(a: CSR, count: int, length: int, seed: int) -> CSR:
+    """``a`` plus ``count`` coupling rows: each chosen row (and, symmetrically, its column)
+    gains ``length`` random off-diagonal entries -U[0,1); every diagonal is then reset to
+    1.01 x its row's off-diagonal absolute sum, so a symmetric diagonally dominant ``a``
+    stays symmetric positive definite.  Irregular (arrow-like) rows of circuit and
+    constraint matrices, for the long-row path."""
+    rng = np.random.default_rng(seed)
+    n = a.n
+    rows = np.repeat(np.arange(n, dtype=np.int64), a.row_lengths())
+    cols = a.colidx.astype(np.int64)
+    off = rows != cols
+    r, c, v = rows[off], cols[off], a.vals[off]
+    hubs = rng.choice(n, size=min(count, n), replace=False)
+    extra_r, extra_c, extra_v = [], [], []
+    for h in hubs:
+        targets = rng.choice(n, size=min(length, n - 1) + 1, replace=False)
+        targets = targets[targets != h][:length]
+        w = -rng.random(targets.size)
+        extra_r += [np.full(targets.size, h), targets]
+        extra_c += [targets, np.full(targets.size, h)]
+        extra_v += [w, w]
+    r = np.concatenate([r] + extra_r)
+    c = np.concatenate([c] + extra_c)
+    v = np.concatenate([v] + extra_v)
+    # merge repeats (a hub pair drawn twice, or an entry already in a)
+    key = r * n + c
+    uk, inv = np.unique(key, return_inverse=True)
+    vv = np.zeros(uk.size)
+    np.add.at(vv, inv, v)
+    r, c, v = uk // n, uk % n, vv
+    diag = np.zeros(n)
+    np.add.at(diag, r, np.abs(v))
+    r = np.concatenate([r, np.arange(n)])
+    c = np.concatenate([c, np.arange(n)])
+    v = np.concatenate([v, 1.01 * diag + (diag == 0)])
+    return _from_coo(n, r, c, v)
+
+
 # ---------------------------------------------------------------- batched workload
 _BATCH_K = (1, 2, 4, 8, 16)
 

@@ -516,3 +516,70 @@ def test_col16_refused_when_the_span_is_too_wide():
     got = gpu_spmv(h, x.cpu().numpy())
     assert_close(got, a, a.vals, x.cpu().numpy())
     csrk.destroy(h)
+
+
+# ------------------------------------------------------------------ long rows
+def long_row_matrix():
+    # 5,100-row 27-point stencil plus three coupling rows of ~4,500 entries each (three
+    # segments of 2,048), under the stencil's random labelling
+    return synth.with_dense_rows(small_27pt(29), 3, 4500, 30)
+
+
+@pytest.mark.parametrize("dtype,kernel", [("f64", 0), ("f64", 1), ("f64", 2), ("f64", 4), ("f32", 0), ("bf16", 4)])
+def test_long_rows_spmv(dtype, kernel):
+    a = long_row_matrix()
+    h = csrk.create(a.n, a.rowptr, a.colidx, a.vals, dtype)
+    csrk.reorder(h)
+    assert csrk.split_long_rows(h, 1000) == 3
+    csrk.set_sizes(h, 32, 4)
+    csrk.set_config(h, kernel=kernel, lanes=1, unroll=8)
+    vals = {"f64": a.vals, "f32": precision.to_f32(a.vals).astype(np.float64),
+            "bf16": precision.bf16_bits_to_f64(precision.to_bf16_bits(a.vals))}[dtype]
+    bound = 1e-12   # against the oracle on the stored (rounded) values
+    x = synth.uniform_vector(a.n, 51)
+    y0 = synth.uniform_vector(a.n, 52)
+    assert_close(gpu_spmv(h, x, 0.75, -1.5, y0), a, vals, x, 0.75, -1.5, y0, bound=bound)
+    if dtype != "f64":   # FP32 vectors and accumulation
+        got = gpu_spmv(h, x.astype(np.float32).astype(np.float64), x_f32=True, acc_f32=True)
+        assert_close(got, a, vals, x.astype(np.float32).astype(np.float64), bound=(np.max(a.row_lengths()) + 2) * 2.0 ** -24)
+    csrk.destroy(h)
+
+
+@pytest.mark.parametrize("k", [2, 5])
+def test_long_rows_spmm(k):
+    a = long_row_matrix()
+    h = csrk.create(a.n, a.rowptr, a.colidx, a.vals)
+    csrk.reorder(h)
+    csrk.split_long_rows(h, 1000)
+    csrk.set_sizes(h, 32, 4)
+    X = synth.uniform_block(a.n, k, 53)
+    Y0 = synth.uniform_block(a.n, k, 54)
+    Xt, Yt = torch.tensor(X, device=DEV), torch.tensor(Y0, device=DEV)
+    csrk.spmm(h, k, 1.5, Xt, k, 0.5, Yt, k)
+    torch.cuda.synchronize()
+    ref = ospmv.csr_spmm(a.n, a.rowptr, a.colidx, a.vals, X, 1.5, 0.5, Y0)
+    got = Yt.cpu().numpy()
+    for c in range(k):
+        s = ospmv.abs_row_scale(a.rowptr, a.colidx, a.vals, X[:, c], 1.5, 0.5, Y0[:, c])
+        assert np.all(np.abs(got[:, c] - ref[:, c]) <= 1e-12 * s)
+    csrk.destroy(h)
+
+
+@pytest.mark.parametrize("inner", ["f64", "f32"])
+def test_long_rows_cg_and_autotune(inner):
+    a = long_row_matrix()
+    h = csrk.create(a.n, a.rowptr, a.colidx, a.vals)
+    csrk.reorder(h)
+    csrk.split_long_rows(h, 1000)
+    csrk.set_sizes(h, 0, 0)                                  # the autotuner times the long rows too
+    b = synth.uniform_vector(a.n, 55)
+    bt = torch.tensor(b, device=DEV)
+    xt = torch.zeros_like(bt)
+    rc, iters, rel = csrk.cg(h, bt, xt, 1e-10, 3000, inner, 20, 0)
+    assert rc == 0 and rel <= 1e-10
+    r = b - ospmv.csr_spmv(a.n, a.rowptr, a.colidx, a.vals, xt.cpu().numpy())
+    assert np.linalg.norm(r) / np.linalg.norm(b) <= 1.05e-10
+    with pytest.raises(csrk.CsrkError) as ei:                # batches take no split rows
+        csrk.batch_create([h], [1])
+    assert ei.value.status == "ERR_UNSUPPORTED"
+    csrk.destroy(h)

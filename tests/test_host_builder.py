@@ -200,3 +200,45 @@ def test_index_bits_follow_the_ssr_column_span():
         csrk.set_sizes(h, 32, 8)
         assert csrk.index_bits(h) == bits, far
         csrk.destroy(h)
+
+
+# ------------------------------------------------------------------ long rows
+def test_split_long_rows_moves_them_last():
+    base = synth.stencil_3d(12, 12, 12, 7, "random_dd", 1, labels=synth.vectors.permutation(1728, 1))
+    a = synth.with_dense_rows(base, 3, 900, 2)
+    long_rows = set(np.nonzero(a.row_lengths() >= 500)[0].tolist())
+    assert len(long_rows) == 3
+    h = csrk.create(a.n, a.rowptr, a.colidx, a.vals)
+    p_rcm = csrk.reorder(h)
+    assert csrk.split_long_rows(h, 500) == 3
+    with pytest.raises(csrk.CsrkError) as ei:             # reordering now would mix them again
+        csrk.reorder(h)
+    assert ei.value.status == "ERR_STATE"
+    csrk.set_sizes(h, 32, 8)
+    e = csrk.export(h)
+    # short rows in RCM order, then the long rows in RCM order
+    expect = [p for p in p_rcm if p not in long_rows] + [p for p in p_rcm if p in long_rows]
+    assert e["perm"].tolist() == expect
+    assert e["sr_ptr"][-1] == a.n - 3 and e["ssr_ptr"][-1] == len(e["sr_ptr"]) - 1
+    rp, ci, v = reorder.permute_loop(a.n, a.rowptr, a.colidx, a.vals, e["perm"])
+    assert np.array_equal(e["rowptr"], rp) and np.array_equal(e["colidx"], ci) and np.array_equal(e["vals"], v)
+    with pytest.raises(csrk.CsrkError) as ei:             # explicit pointers must stop at n - n_long
+        csrk.set_pointers(h, [0, a.n], [0, 1])
+    assert ei.value.status == "ERR_ARG"
+    csrk.set_pointers(h, [0, a.n - 3], [0, 1])
+    csrk.destroy(h)
+
+
+def test_split_long_rows_arguments_and_no_long_rows():
+    a = synth.stencil_2d_5pt(10, 10)
+    h = csrk.create(a.n, a.rowptr, a.colidx, a.vals)
+    with pytest.raises(csrk.CsrkError) as ei:
+        csrk.split_long_rows(h, 0)
+    assert ei.value.status == "ERR_ARG"
+    assert csrk.split_long_rows(h, 6) == 0                 # 5-point rows: nothing moves
+    csrk.set_sizes(h, 8, 2)
+    assert np.array_equal(csrk.export(h)["perm"], np.arange(a.n))
+    with pytest.raises(csrk.CsrkError) as ei:
+        csrk.split_long_rows(h, 3)
+    assert ei.value.status == "ERR_STATE"
+    csrk.destroy(h)
