@@ -545,6 +545,44 @@ def run_batch(args, dev, stream, peak):
     return out
 
 
+# ------------------------------------------------------------------ irregular matrices
+def run_irregular(args, dev):
+    """A 100^3 7-point stencil (random labels) plus 16 coupling rows of 100,000 entries:
+    SpMV (natural numbering, fused unpermute) with the long rows left in the super-rows
+    versus moved out by csrk_split_long_rows, both autotuned."""
+    import torch
+    from paper_2203_05096_gb300 import csrk
+    side = 100
+    n = side ** 3
+    base = synth.stencil_3d(side, side, side, 7, "random_dd", 3, labels=synth.vectors.permutation(n, 3))
+    a = synth.with_dense_rows(base, 16, 100_000, 7)
+    x = torch.tensor(synth.uniform_vector(n, 2), dtype=torch.float64, device=dev)
+    y = torch.empty_like(x)
+    stream = torch.cuda.current_stream(dev)
+    out = {"workload": "100^3 7-point stencil + 16 coupling rows of 100,000 entries (random labels)",
+           "n": n, "nnz": int(a.nnz), "max_row": int(a.row_lengths().max())}
+    for mode in ("in_super_rows", "split"):
+        h = csrk.create(a.n, a.rowptr, a.colidx, a.vals)
+        csrk.reorder(h, "rcm", want_perm=False)
+        nl = csrk.split_long_rows(h, 4096) if mode == "split" else 0
+        csrk.set_sizes(h, 0, 0)
+        for _ in range(5):
+            csrk.spmv(h, 1.0, x, 0.0, y)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(50):
+            csrk.spmv(h, 1.0, x, 0.0, y)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        us = e0.elapsed_time(e1) / 50 * 1e3
+        out[mode] = {"us": round(us, 2), "gflops": round(2.0 * a.nnz / (us * 1e-6) / 1e9, 1), "long_rows": nl,
+                     "config": csrk.tuned_config(h)}
+        csrk.destroy(h)
+    out["speedup"] = round(out["in_super_rows"]["us"] / out["split"]["us"], 2)
+    return out
+
+
 # ------------------------------------------------------------------ reference arm
 def run_reference(args, world, rank, local):
     """The FP64 CPU oracle as it stands, on the host cores, each step a bounded block of
@@ -622,10 +660,17 @@ def main():
     p.add_argument("--bandk-caps", default="32,4", help="Band-k caps 'sr,ssr'")
     p.add_argument("--batch-only", action="store_true",
                    help="run only the batched section (profiling); prints {'batch': ...}")
+    p.add_argument("--irregular", action="store_true",
+                   help="run only the long-row comparison; prints {'irregular': ...}")
     args = p.parse_args()
     if args.warmup < 3:
         p.error("--warmup must be >= 3")
     world, rank, local = dist_env()
+    if args.irregular:
+        import torch
+        torch.cuda.set_device(local)
+        print(json.dumps({"irregular": run_irregular(args, torch.device("cuda", local))}), flush=True)
+        return
     if args.batch_only:
         import torch
         torch.cuda.set_device(local)

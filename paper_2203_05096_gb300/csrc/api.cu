@@ -648,7 +648,9 @@ int autotune(csrk_matrix* h) {
                                                       {64, 1}, {64, 2}, {64, 4}, {64, 8}, {128, 1},
                                                       {128, 2}, {16, 4}, {16, 8}, {16, 16}};
     int32_t model_ssrs = 0, model_srs = 0;
-    const double rdens = (double)h->m.nnz() / h->m.n;
+    // mean row length over the rows the super-rows cover (split long rows excluded)
+    const int32_t n_cov = h->m.n - h->n_long;
+    const double rdens = n_cov > 0 ? (double)h->m.rowptr[n_cov] / n_cov : 0.0;
     if (rdens > 0 && csrk_model_sizes(rdens, 1, &model_ssrs, &model_srs) == CSRK_OK && model_srs > 0 &&
         model_ssrs > 0)
         sizes.emplace_back(model_srs, model_ssrs);
@@ -671,10 +673,18 @@ int autotune(csrk_matrix* h) {
     std::sort(phase1.begin(), phase1.end(), [](auto& a, auto& b) { return a.us < b.us; });
     TunedChoice best = phase1.empty() ? TunedChoice{} : phase1.front();
 
-    std::vector<std::pair<int, int>> pairs;
-    if (rdens <= 32) pairs = {{1, 4}, {1, 8}, {1, 16}, {2, 8}};
-    else if (rdens <= 64) pairs = {{2, 8}, {2, 16}, {4, 8}};
-    else pairs = {{4, 8}, {8, 8}, {32, 4}};
+    // lane counts for the mean row length, and -- for irregular matrices, whose longest
+    // super-row row decides how long a warp pass takes -- for the longest row as well
+    auto pairs_for = [](double len) -> std::vector<std::pair<int, int>> {
+        if (len <= 32) return {{1, 4}, {1, 8}, {1, 16}, {2, 8}};
+        if (len <= 64) return {{2, 8}, {2, 16}, {4, 8}};
+        if (len <= 256) return {{4, 8}, {8, 8}, {32, 4}};
+        return {{8, 8}, {32, 4}};
+    };
+    std::vector<std::pair<int, int>> pairs = pairs_for(rdens);
+    if (h->stats.max_row_len > 4 * rdens)
+        for (auto& p : pairs_for(h->stats.max_row_len))
+            if (std::find(pairs.begin(), pairs.end(), p) == pairs.end()) pairs.push_back(p);
     const bool with_pairs = pairs_available(h);
     std::vector<TunedChoice> phase2;
     for (size_t b = 0; b < std::min<size_t>(3, phase1.size()) && rc == CSRK_OK; ++b) {
