@@ -109,7 +109,7 @@ int csrk_create(int32_t n, const int32_t* rowptr, const int32_t* colidx, const d
  * Host only. */
 int csrk_reorder(csrk_handle h, int method, int32_t* perm_out);
 
-/* csrk_reorder_bandk: the Band-k ordering for k = 3 (Sec. 2.3, Listing 2, Fig. 2): the
+/* csrk_reorder_bandk: the Band-k ordering for k = 3 (Sec. 2.2, Listing 2, Fig. 2): the
  * rows are coarsened into super-rows of at most sr rows and those into super-super-rows
  * of at most ssr super-rows, the coarse levels are put in weighted bandwidth-limiting
  * order and expanded again; the renumbering and the (variable) pointer arrays are

@@ -1,6 +1,6 @@
 """Oracle Band-k ordering (TEST INFRASTRUCTURE).
 
-Sec. 2.3 (Listing 2, Fig. 2) describes Band-k, the CSR-k ordering for SpMV: the matrix
+Sec. 2.2 (Listing 2, Fig. 2) describes Band-k, the CSR-k ordering for SpMV: the matrix
 graph is coarsened level by level, each coarse level is put in a weighted
 bandwidth-limiting order, the coarse nodes are expanded again with the vertices inside
 each coarse node reordered by a bandwidth-limiting order, and the coarse nodes of the

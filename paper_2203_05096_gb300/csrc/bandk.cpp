@@ -1,4 +1,4 @@
-// Band-k ordering for k = 3 (rows, super-rows, super-super-rows): Sec. 2.3, Listing 2.
+// Band-k ordering for k = 3 (rows, super-rows, super-super-rows): Sec. 2.2, Listing 2.
 //
 // The paper coarsens the matrix graph level by level, puts each coarse level in a
 // weighted bandwidth-limiting order, expands the coarse nodes again reordering the

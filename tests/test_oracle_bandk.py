@@ -1,4 +1,4 @@
-"""Pins for the oracle's Band-k ordering (reading of Sec. 2.3, Listing 2)."""
+"""Pins for the oracle's Band-k ordering (reading of Sec. 2.2, Listing 2)."""
 import numpy as np
 import pytest
 
