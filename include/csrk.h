@@ -206,7 +206,7 @@ int csrk_permute(csrk_handle h, int direction, int32_t k, const void* in, int64_
                  void* out, int64_t ldo, unsigned flags, void* stream);
 
 /* csrk_cg: solve A x = b for symmetric positive definite A by conjugate gradients on the
- * CSR-k form (the paper names CG as the SpMV's consumer: Sec. 1, Sec. 7, Sec. 8), with
+ * CSR-k form (the paper names CG as the SpMV's consumer: Sec. 1, 5.3, 8, 9), with
  * x0 = 0 and the Hestenes-Stiefel recurrences.
  *   b, x          DEVICE FP64 vectors of n entries, input numbering unless
  *                 CSRK_VEC_PERMUTED; x receives the solution

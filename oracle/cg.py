@@ -1,6 +1,6 @@
 """Oracle conjugate gradients, FP64 and mixed precision (TEST INFRASTRUCTURE).
 
-The paper names CG on PDE matrices as the consumer of its SpMV (Sec. 1, Sec. 7, Sec. 8);
+The paper names CG on PDE matrices as the consumer of its SpMV (Sec. 1, Sec. 5.3, Sec. 8, Sec. 9);
 the library adds an FP64 CG and a mixed-precision CG on top of its kernels.  The reading
 used by both this oracle and the library:
 

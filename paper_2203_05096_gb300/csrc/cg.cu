@@ -1,7 +1,7 @@
 // Conjugate gradients on the CSR-k form, FP64 or mixed precision, with iterations
 // captured in CUDA graphs.
 //
-// The paper names CG on PDE matrices as the consumer of its SpMV (Sec. 1, Sec. 7, Sec. 8).
+// The paper names CG on PDE matrices as the consumer of its SpMV (Sec. 1, Sec. 5.3, Sec. 8, Sec. 9).
 // Recurrences (Hestenes-Stiefel): x0 = 0, r0 = b, p0 = r0;
 //     q = A p;  alpha = r.r / p.q;  x += alpha p;  r -= alpha q;
 //     beta = r'.r' / r.r;  p = r' + beta p.
