@@ -593,7 +593,9 @@ void save_tune_entry(const std::string& key, const TunedChoice& c) {
 }
 
 float time_launches(csrk_matrix* h, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1, int reps) {
-    const unsigned fl = CSRK_VEC_PERMUTED;
+    // a reordered handle is timed as its natural-numbering call runs: x already permuted,
+    // y stored through the permutation by the kernel (the fused unpermute)
+    const unsigned fl = h->perm.empty() ? CSRK_VEC_PERMUTED : CSRK_X_PERMUTED;
     for (int i = 0; i < 2; ++i)
         if (compute(h, 1, false, 1.0, h->d_scratch[0], 1, 0.0, h->d_scratch[1], 1, fl, s)) return 1e30f;
     cudaEventRecord(e0, s);
