@@ -1053,7 +1053,8 @@ int csrk_batch_spmm(csrk_batch_handle b, double alpha, const void* const* X, dou
         // the pinned staging table may still feed an earlier copy: wait for it first
         CK_CUDA(cudaStreamSynchronize(s), "synchronise");
         for (int32_t i = 0; i < b->nmat; ++i) {
-            if (!X[i] || !Y[i] || X[i] == Y[i]) return fail(CSRK_ERR_ARG, "bad vector pointer");
+            if (b->h_mats[i].n > 0 && (!X[i] || !Y[i] || X[i] == Y[i]))   // empty matrices may pass NULL
+                return fail(CSRK_ERR_ARG, "bad vector pointer");
             pinned[i] = b->h_mats[i];
             if (xt && b->hs[i]->dtype == CSRK_F64) {
                 pinned[i].vals = b->hs[i]->d_vals[csrk::VAL_F32];

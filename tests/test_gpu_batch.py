@@ -303,3 +303,28 @@ def test_batch_cg_solve_iteration_limit_and_fallback(monkeypatch):
     csrk.batch_destroy(b)
     for h in hs:
         csrk.destroy(h)
+
+
+def test_batch_with_an_empty_matrix():
+    specs = [(synth.stencil_3d(9, 8, 7, 7, "random_dd", 70), "f64", 2, (32, 4)),
+             (synth.CSR(0, np.zeros(1, np.int32), np.zeros(0, np.int32), np.zeros(0)), "f64", 4, (32, 4)),
+             (synth.stencil_2d_5pt(11, 9), "f32", 1, (16, 2))]
+    hs, forms = make_batch(specs)
+    b = csrk.batch_create(hs, [k for _, _, k, _ in specs])
+    Xs = [torch.tensor(synth.uniform_block(a.n, k, 71 + i), device=DEV).reshape(a.n, k) for i, (a, _, k, _) in enumerate(specs)]
+    Ys = [torch.zeros_like(x) for x in Xs]
+    csrk.batch_spmm(b, 1.0, Xs, 0.0, Ys)
+    torch.cuda.synchronize()
+    for i, ((a, _, k, _), (rp, ci, v)) in enumerate(zip(specs, forms)):
+        if a.n == 0:
+            continue
+        X = Xs[i].cpu().numpy()
+        ref = ospmv.csr_spmm(a.n, rp, ci, v, X)
+        assert np.allclose(Ys[i].cpu().numpy(), ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+    Bs = [torch.tensor(synth.uniform_block(a.n, k, 81 + i), device=DEV).reshape(a.n, k) for i, (a, _, k, _) in enumerate(specs)]
+    Xc = [torch.zeros_like(x) for x in Bs]
+    rc, rel, its, _ = csrk.batch_cg_solve(b, Bs, Xc, rtol=1e-10, maxit=2000, inner="f32")
+    assert rc == 0 and np.all(rel <= 1e-10)
+    csrk.batch_destroy(b)
+    for h in hs:
+        csrk.destroy(h)

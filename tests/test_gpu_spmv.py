@@ -583,3 +583,47 @@ def test_long_rows_cg_and_autotune(inner):
         csrk.batch_create([h], [1])
     assert ei.value.status == "ERR_UNSUPPORTED"
     csrk.destroy(h)
+
+
+# ------------------------------------------------------------------ degenerate shapes of the newer paths
+def test_col16_with_bandk_pointers_and_empty_rows():
+    a = synth.random_pattern(3000, 0.002, 61, symmetric=True, empty_rows=200)
+    h = csrk.create(a.n, a.rowptr, a.colidx, a.vals)
+    csrk.reorder_bandk(h, 16, 3)
+    assert csrk.index_bits(h) == 16
+    x = synth.uniform_vector(a.n, 62)
+    out = []
+    for kernel in (0, 4):
+        csrk.set_config(h, kernel=kernel, lanes=1, unroll=4, warps=8)
+        out.append(gpu_spmv(h, x))
+    assert np.array_equal(out[0], out[1])
+    assert_close(out[1], a, a.vals, x)
+    csrk.destroy(h)
+
+
+@pytest.mark.parametrize("lengths", [(2048, 2049, 4096), (1, 1, 1)])
+def test_long_rows_segment_boundaries_and_all_rows_long(lengths):
+    """Rows of exactly one segment, one entry over, two full segments; and a threshold of
+    1 that moves every row out of the super-rows (no SSR at all)."""
+    rng = np.random.default_rng(63)
+    n = 5000
+    rows = [sorted(set([i] + rng.choice(n, 3, replace=False).tolist())) for i in range(n)]
+    for r, L in zip((7, 1234, 4999), lengths):
+        if L > 1:
+            rows[r] = sorted(set([r] + rng.choice(n, L - 1, replace=False).tolist()))
+            while len(rows[r]) < L:
+                rows[r] = sorted(set(rows[r] + rng.choice(n, L - len(rows[r]), replace=False).tolist()))
+    rp = np.array([0] + np.cumsum([len(r) for r in rows]).tolist(), np.int32)
+    ci = np.array([c for r in rows for c in r], np.int32)
+    vals = rng.standard_normal(ci.size)
+    a = synth.CSR(n, rp, ci, vals)
+    h = csrk.create(n, rp, ci, vals)
+    thr = 2048 if lengths[0] > 1 else 1
+    nl = csrk.split_long_rows(h, thr)
+    assert nl == (3 if thr > 1 else n)
+    csrk.set_sizes(h, 32, 4)
+    assert csrk.info(h)["nssr"] == (0 if thr == 1 else csrk.info(h)["nssr"])
+    x = synth.uniform_vector(n, 64)
+    y0 = synth.uniform_vector(n, 65)
+    assert_close(gpu_spmv(h, x, -1.0, 2.0, y0), a, vals, x, -1.0, 2.0, y0)
+    csrk.destroy(h)
