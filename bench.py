@@ -54,15 +54,21 @@ MATRICES = (("stencil7", 7), ("stencil27", 27))
 # nonzeros.
 NCU_TRAFFIC = {
     ("stencil27", "f64", 0): {"bytes": 712_940_980, "kernel_hash": "871b5d682a86"},
-    ("stencil27", "f64", 4): {"bytes": 601_073_144, "kernel_hash": "6685092d4e31"},
+    ("stencil27", "f64", 4): {"bytes": 601_073_144, "kernel_hash": "150e04d362cd"},
 }
 
 
 def kernel_source_hash() -> str:
+    """Hash of the FP64 SpMV kernel sources with comments and blank space removed, so that
+    a comment edit does not orphan a capture of unchanged code."""
+    import re
     h = hashlib.sha1()
     for f in ("kernels.cuh", "launch_impl.cuh", "spmv_f64.cu"):
-        with open(os.path.join(ROOT, "paper_2203_05096_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2203_05096_gb300", "csrc", f)) as fh:
+            src = fh.read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        h.update(" ".join(src.split()).encode())
     return h.hexdigest()[:12]
 
 

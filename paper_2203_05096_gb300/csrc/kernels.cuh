@@ -13,7 +13,10 @@
 // four contiguous byte ranges.  In the TMA kernel a producer warp copies them into a
 // ring of shared-memory stages with cp.async.bulk (completion counted by an mbarrier,
 // L2 evict-first hint so that x stays resident in L2), S-1 SSRs ahead of the consumers.
-// x is gathered through the read-only path; y is written once per row.
+// The column slice is int32, or (MODE 3) delta-coded 16-bit steps rebuilt by the lanes.
+// x is gathered through the read-only path; y is written once per row, through the
+// permutation when the unpermute is fused.  Rows split off as long rows are not in any
+// SSR (long_rows.cu computes them).
 //
 // GB300 note: FP64 FMA runs at about 2 per clock per SM here, so the FP64 path spends
 // exactly one FP64 instruction per nonzero: narrow values are widened with integer
