@@ -2,6 +2,7 @@
 // upload of the CSR-k form, library-owned scratch vectors, launch configuration and the
 // permute -> CSR-3 kernel -> unpermute sequence of a compute call.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -38,6 +39,16 @@ void csrk::set_last_error(const std::string& msg) { csrk::rt::g_last_error = msg
 
 namespace csrk {
 namespace rt {
+
+bool fault_injected(const char* step) {
+    const char* f = std::getenv("CSRK_FAULT");
+    if (!f || !*f) return false;
+    const std::string list = std::string(",") + f + ",";
+    return list.find(std::string(",") + step + ",") != std::string::npos;
+}
+
+NvtxRange::NvtxRange(const char* name) { nvtxRangePushA(name); }
+NvtxRange::~NvtxRange() { nvtxRangePop(); }
 
 void free_ptrs(csrk_matrix* h) {
     cudaFree(h->d_sr_ptr);
@@ -88,10 +99,15 @@ template <typename T>
 int upload_padded(T** dst, const void* src, size_t count, size_t esz, const char* what) {
     const size_t bytes = (count + 16) * esz;
     void* p = nullptr;
+    if (fault_injected("alloc")) return fail(CSRK_ERR_ALLOC, std::string("cudaMalloc ") + what + ": injected fault");
     cudaError_t e = cudaMalloc(&p, bytes);
     if (e != cudaSuccess) return fail(CSRK_ERR_ALLOC, std::string("cudaMalloc ") + what + ": " + cudaGetErrorString(e));
     e = cudaMemset(p, 0, bytes);
     if (e == cudaSuccess && count) e = cudaMemcpy(p, src, count * esz, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && fault_injected("h2d")) {
+        cudaFree(p);
+        return fail(CSRK_ERR_CUDA, std::string(what) + ": injected copy fault");
+    }
     if (e != cudaSuccess) {
         cudaFree(p);
         return cuda_fail(e, what);
@@ -123,6 +139,7 @@ int ensure_struct(csrk_matrix* h) {
     const CsrHost& m = h->m;
     int rc;
     if (!h->dev_struct) {
+        NvtxRange range("csrk upload");
         if ((rc = upload_padded(&h->d_rowptr, m.rowptr.data(), m.rowptr.size(), 4, "rowptr"))) return rc;
         if ((rc = upload_padded(&h->d_colidx, m.colidx.data(), m.colidx.size(), 4, "colidx"))) return rc;
         if (!h->perm.empty())
@@ -168,6 +185,7 @@ int ensure_scratch(csrk_matrix* h, int slot, size_t bytes) {
     cudaFree(h->d_scratch[slot]);
     h->d_scratch[slot] = nullptr;
     h->scratch_bytes[slot] = 0;
+    if (fault_injected("alloc")) return fail(CSRK_ERR_ALLOC, "cudaMalloc scratch: injected fault");
     void* p = nullptr;
     cudaError_t e = cudaMalloc(&p, bytes);
     if (e != cudaSuccess) return fail(CSRK_ERR_ALLOC, std::string("cudaMalloc scratch: ") + cudaGetErrorString(e));
@@ -610,6 +628,8 @@ float time_launches(csrk_matrix* h, cudaStream_t s, cudaEvent_t e0, cudaEvent_t 
 
 int autotune(csrk_matrix* h) {
     int rc;
+    NvtxRange range("csrk autotune");
+    if (fault_injected("tune")) return fail(CSRK_ERR_CUDA, "autotuning: injected fault");
     // Band-k pointers in place: tune the launch shape only, on those pointers
     const bool bandk = h->have_ptrs && h->bandk_sr > 0;
     if (h->m.n == 0) return bandk ? CSRK_OK : set_fixed(h, 32, 8);
@@ -760,6 +780,7 @@ extern "C" {
 int csrk_create(int32_t n, const int32_t* rowptr, const int32_t* colidx, const double* vals,
                 csrk_dtype dtype, csrk_handle* out) {
     if (!out) return fail(CSRK_ERR_ARG, "out is NULL");
+    NvtxRange range("csrk create");
     *out = nullptr;
     if (dtype != CSRK_F64 && dtype != CSRK_F32 && dtype != CSRK_BF16)
         return fail(CSRK_ERR_ARG, "unknown dtype");
@@ -783,6 +804,7 @@ int csrk_create(int32_t n, const int32_t* rowptr, const int32_t* colidx, const d
 
 int csrk_reorder(csrk_handle h, int method, int32_t* perm_out) {
     if (!h) return fail(CSRK_ERR_ARG, "handle is NULL");
+    NvtxRange range("csrk reorder");
     if (h->have_ptrs) return fail(CSRK_ERR_STATE, "reorder must come before csrk_set_sizes / csrk_set_pointers");
     if (h->n_long > 0) return fail(CSRK_ERR_STATE, "reorder must come before csrk_split_long_rows");
     if (method != CSRK_REORDER_NONE && method != CSRK_REORDER_RCM) return fail(CSRK_ERR_ARG, "unknown method");
@@ -812,6 +834,7 @@ int csrk_reorder(csrk_handle h, int method, int32_t* perm_out) {
 
 int csrk_reorder_bandk(csrk_handle h, int32_t sr, int32_t ssr, int32_t* perm_out) {
     if (!h) return fail(CSRK_ERR_ARG, "handle is NULL");
+    NvtxRange range("csrk reorder band-k");
     if (h->have_ptrs) return fail(CSRK_ERR_STATE, "reorder must come before csrk_set_sizes / csrk_set_pointers");
     if (h->n_long > 0) return fail(CSRK_ERR_STATE, "Band-k does not take split long rows");
     if (sr < 1 || ssr < 1) return fail(CSRK_ERR_ARG, "sr and ssr must be >= 1");
@@ -843,6 +866,7 @@ int csrk_reorder_bandk(csrk_handle h, int32_t sr, int32_t ssr, int32_t* perm_out
 
 int csrk_split_long_rows(csrk_handle h, int32_t min_len, int32_t* n_long) {
     if (!h) return fail(CSRK_ERR_ARG, "handle is NULL");
+    NvtxRange range("csrk split long rows");
     if (h->have_ptrs) return fail(CSRK_ERR_STATE, "split long rows before csrk_set_sizes / csrk_set_pointers");
     if (min_len < 1) return fail(CSRK_ERR_ARG, "min_len must be >= 1");
     try {
@@ -885,6 +909,7 @@ int csrk_split_long_rows(csrk_handle h, int32_t min_len, int32_t* n_long) {
 namespace {
 int install_pointers_impl(csrk_handle h, std::vector<int32_t>&& srp, std::vector<int32_t>&& ssrp) {
     std::string err;
+    NvtxRange range("csrk pointers");
     if (!check_pointers(h->m.n - h->n_long, srp, ssrp, err)) return fail(CSRK_ERR_ARG, err);
     h->sr_ptr = std::move(srp);
     h->ssr_ptr = std::move(ssrp);

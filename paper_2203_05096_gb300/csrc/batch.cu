@@ -760,6 +760,7 @@ using namespace csrk::rt;
 
 template <typename T>
 int dmalloc(T** p, size_t count) {
+    if (fault_injected("alloc")) return fail(CSRK_ERR_ALLOC, "batch cudaMalloc: injected fault");
     cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), std::max<size_t>(count, 1) * sizeof(T));
     return e == cudaSuccess ? CSRK_OK : fail(CSRK_ERR_ALLOC, std::string("batch cudaMalloc: ") + cudaGetErrorString(e));
 }
@@ -836,6 +837,7 @@ extern "C" {
 
 int csrk_batch_create(const csrk_handle* hs, int32_t count, const int32_t* k, csrk_batch_handle* out) {
     if (!out || !hs || !k || count < 1) return fail(CSRK_ERR_ARG, "bad batch arguments");
+    NvtxRange range("csrk batch create");
     *out = nullptr;
     csrk_batch* b = new (std::nothrow) csrk_batch();
     if (!b) return fail(CSRK_ERR_ALLOC, "out of host memory");
@@ -1237,6 +1239,7 @@ int csrk_batch_cg_solve(csrk_batch_handle b, const double* const* B, double* con
     if (mixed && b->stages < 2)
         return fail(CSRK_ERR_UNSUPPORTED, "mixed-precision batched CG needs the staged SpMM kernel "
                                           "(super-rows too large for two shared-memory stages)");
+    NvtxRange range("csrk batch cg solve");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     int rc;
     if ((rc = bcg_workspace(b))) return rc;

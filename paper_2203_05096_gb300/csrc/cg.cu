@@ -431,6 +431,7 @@ int alloc_cg(csrk_matrix* h) {
     w->n = n;
     const size_t d = (size_t)std::max(n, 1) * 8, f = (size_t)std::max(n, 1) * 4;
     cudaError_t e = cudaSuccess;
+    if (fault_injected("alloc")) e = cudaErrorMemoryAllocation;
     if (e == cudaSuccess) e = cudaMalloc(&w->b, d);
     if (e == cudaSuccess) e = cudaMalloc(&w->x, d);
     if (e == cudaSuccess) e = cudaMalloc(&w->r, d);
@@ -490,6 +491,7 @@ int cg_solve(csrk_matrix* h, const double* b, double* x, double rtol, int32_t ma
              int32_t every, int32_t restart, unsigned flags, int32_t* iters, double* relres,
              cudaStream_t s) {
     int rc;
+    NvtxRange range("csrk cg");
     if ((rc = ensure_context(h)) || (rc = ensure_struct(h)) || (rc = ensure_vals(h, VAL_F64))) return rc;
     if (vt != VAL_F64 && (rc = ensure_vals(h, vt))) return rc;
     if ((rc = alloc_cg(h))) return rc;

@@ -67,6 +67,18 @@ struct csrk_matrix {
 namespace csrk {
 namespace rt {
 
+// Host-side fault injection for tests: CSRK_FAULT names steps that should fail as if the
+// CUDA call behind them had ("alloc": device allocations -> CSRK_ERR_ALLOC; "h2d": uploads
+// of the matrix -> CSRK_ERR_CUDA; "tune": the autotuner -> CSRK_ERR_CUDA).  Nothing is
+// injected on the device.
+bool fault_injected(const char* step);
+
+// NVTX range around a host-side stage (visible in a profiler's timeline; a no-op otherwise).
+struct NvtxRange {
+    explicit NvtxRange(const char* name);
+    ~NvtxRange();
+};
+
 int fail(int code, const std::string& msg);
 int cuda_fail(cudaError_t e, const char* what);
 size_t val_size(int vt);
