@@ -27,10 +27,18 @@
  *     them on first use (the first compute call after csrk_set_sizes / csrk_set_pointers,
  *     or the first call that needs a larger scratch size) on the device current at that
  *     time; later calls must be made with the same device current.
- *   - Life cycle: csrk_create -> [csrk_reorder] -> csrk_set_sizes or csrk_set_pointers
- *     -> compute calls ...; csrk_set_sizes may be called again (the pointer arrays and
- *     device copies are rebuilt); csrk_reorder after the pointers exist returns
+ *   - Life cycle: csrk_create -> [csrk_reorder | csrk_reorder_bandk] ->
+ *     [csrk_split_long_rows] -> csrk_set_sizes or csrk_set_pointers (Band-k installs its
+ *     own) -> compute calls ...; csrk_set_sizes may be called again (the pointer arrays
+ *     and device copies are rebuilt); csrk_reorder after the pointers exist returns
  *     CSRK_ERR_STATE.  A handle is not thread-safe: one thread uses it at a time.
+ *   - Environment: CSRK_TUNE_CACHE names a file that keeps the autotuner's choices across
+ *     processes; CSRK_BATCH_ITEM_BYTES overrides the batched kernel's item size;
+ *     CSRK_FAULT (tests) makes host-side steps fail as if their CUDA call had: "alloc"
+ *     (device allocations, CSRK_ERR_ALLOC), "h2d" (matrix uploads, CSRK_ERR_CUDA), "tune"
+ *     (the autotuner, CSRK_ERR_CUDA), comma-separated.
+ *   - The host stages (create, reorder, pointers, upload, autotune, solvers) are marked
+ *     with NVTX ranges named "csrk ...".
  */
 #ifndef CSRK_H
 #define CSRK_H
