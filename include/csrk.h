@@ -78,7 +78,11 @@ typedef enum {
 #define CSRK_X_F32        4u  /* x and y are FP32 (default FP64) */
 #define CSRK_HOST_VECTORS 8u  /* x and y are HOST pointers: the call copies x in and y out
                                  through its own device scratch and returns after the
-                                 copy of y has completed (synchronous) */
+                                 copy of y has completed (synchronous).  A page-locked x
+                                 (cudaHostAlloc / cudaHostRegister, mapped) that needs
+                                 permuting is read by the permute kernel directly over the
+                                 host link, one pass instead of copy + permute; the library
+                                 then keeps the inverse permutation on the device (4n bytes) */
 #define CSRK_X_PERMUTED  16u  /* SpMV only: x is already in the reordered numbering (e.g.
                                  from csrk_permute), y is in the input numbering; the kernel
                                  writes row r's result to y[perm[r]] directly */

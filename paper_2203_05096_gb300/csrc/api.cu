@@ -72,7 +72,8 @@ void free_struct(csrk_matrix* h) {
     h->d_col16 = nullptr;
     h->col16_ok = -1;
     cudaFree(h->d_perm);
-    h->d_rowptr = h->d_colidx = h->d_perm = nullptr;
+    cudaFree(h->d_iperm);
+    h->d_rowptr = h->d_colidx = h->d_perm = h->d_iperm = nullptr;
     h->dev_struct = false;
 }
 
@@ -192,6 +193,26 @@ int ensure_scratch(csrk_matrix* h, int slot, size_t bytes) {
     h->d_scratch[slot] = p;
     h->scratch_bytes[slot] = bytes;
     return CSRK_OK;
+}
+
+// Inverse of perm (iperm[old] = new) on the device, for the permute that reads a
+// page-locked host x in its own order and scatters it into the reordered numbering.
+int ensure_iperm(csrk_matrix* h) {
+    if (h->d_iperm || h->perm.empty()) return CSRK_OK;
+    std::vector<int32_t> inv(h->perm.size());
+    for (size_t i = 0; i < h->perm.size(); ++i) inv[(size_t)h->perm[i]] = (int32_t)i;
+    return upload_padded(&h->d_iperm, inv.data(), inv.size(), 4, "inverse permutation");
+}
+
+// Device address of a page-locked, mapped host pointer (cudaHostAlloc, cudaHostRegister);
+// NULL for pageable memory, whose contents go through cudaMemcpyAsync instead.
+const void* mapped_host_ptr(const void* p) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
 }
 
 int default_lanes(const csrk_matrix* h) {
@@ -403,14 +424,22 @@ int compute(csrk_matrix* h, int32_t k, bool spmm, double alpha, const void* X, i
     const void* xin = X;
     void* yout = Y;
     int64_t ldxin = ldx, ldyout = ldy;
+    // a page-locked host x that needs permuting is read by the permute kernel itself over
+    // the host link (in x's own order, scattered through the inverse permutation), so the
+    // copy and the permute are one pass instead of two
+    const void* x_mapped = nullptr;
     if (host_vec) {
         const size_t xb = (size_t)n * ldx * esz, yb = (size_t)n * ldy * esz;
-        if ((rc = ensure_scratch(h, 2, xb))) return rc;
+        if (!permuted && !x_only && !pairs) x_mapped = mapped_host_ptr(X);
+        if (x_mapped && (rc = ensure_iperm(h))) return rc;
+        if (!x_mapped && (rc = ensure_scratch(h, 2, xb))) return rc;
         if ((rc = ensure_scratch(h, 3, yb))) return rc;
-        CK_CUDA(cudaMemcpyAsync(h->d_scratch[2], X, xb, cudaMemcpyHostToDevice, s), "copy x to device");
+        if (!x_mapped) {
+            CK_CUDA(cudaMemcpyAsync(h->d_scratch[2], X, xb, cudaMemcpyHostToDevice, s), "copy x to device");
+            xin = h->d_scratch[2];
+        }
         if (beta != 0.0)
             CK_CUDA(cudaMemcpyAsync(h->d_scratch[3], Y, yb, cudaMemcpyHostToDevice, s), "copy y to device");
-        xin = h->d_scratch[2];
         yout = h->d_scratch[3];
     }
     const void* xk = xin;
@@ -423,7 +452,10 @@ int compute(csrk_matrix* h, int32_t k, bool spmm, double alpha, const void* X, i
         const size_t b = (size_t)n * k * esz;
         if ((rc = ensure_scratch(h, 0, b))) return rc;
         if (!fuse_y && (rc = ensure_scratch(h, 1, b))) return rc;
-        if (!pairs) {
+        if (x_mapped) {
+            int e = launch_scatter_rows(x_mapped, ldxin, h->d_scratch[0], k, h->d_iperm, n, k, (int)esz, s);
+            if (e) return cuda_fail((cudaError_t)e, "permute host x");
+        } else if (!pairs) {
             int e = launch_gather_rows(xin, ldxin, h->d_scratch[0], k, h->d_perm, n, k, (int)esz, s);
             if (e) return cuda_fail((cudaError_t)e, "permute x");
         }

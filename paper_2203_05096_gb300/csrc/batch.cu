@@ -474,8 +474,10 @@ __global__ void __launch_bounds__(VT_THREADS) bcg_init(const Chunk* __restrict__
     chunk_partial(v, k, partials + (int64_t)blockIdx.x * 32);
 }
 
+// FP32 -> FP64 with integer instructions (exact, like the conversion instruction, which
+// would take a slot of GB300's narrow FP64 pipe)
 __device__ __forceinline__ double as_f64(double v) { return v; }
-__device__ __forceinline__ double as_f64(float v) { return (double)v; }
+__device__ __forceinline__ double as_f64(float v) { return csrk::dev::x_f64(v); }
 
 // The hot vector kernels walk a chunk CHUNK_ILP elements per thread per trip (e, e + 256,
 // ...), issuing all of a trip's loads before any arithmetic, so each thread keeps several

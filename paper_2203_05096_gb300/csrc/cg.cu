@@ -62,6 +62,12 @@ __device__ __forceinline__ void ld2q(const double* q, int64_t j, double& a, doub
     b = v.y;
 }
 __device__ __forceinline__ void ld2q(const float* q, int64_t j, double& a, double& b);
+// part + a*b + c*d as two chained FMAs: GB300 issues FP64 at about one warp instruction
+// per 20 clocks per SM whatever the active lanes, so the vector passes count FP64
+// instructions as well as bytes (a*b + c*d + part would take three)
+__device__ __forceinline__ double fma2(double part, double a, double b, double c, double d) {
+    return fma(c, d, fma(a, b, part));
+}
 __device__ __forceinline__ void st2f(float* p, int64_t j, double a, double b) {
     reinterpret_cast<float2*>(p)[j] = make_float2((float)a, (float)b);
 }
@@ -90,16 +96,19 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-// Block sum of v; the block total is returned to thread 0.
+// Block sum of v; the block total is returned to thread 0.  Warp 0 alone adds: each lane
+// sums a fixed strided eighth of the block's values, then one shuffle tree -- 12 FP64 warp
+// instructions per block instead of 45 for a shuffle tree in every warp (on GB300 an FP64
+// instruction costs the same with one active lane as with 32).
 __device__ double block_sum(double v) {
-    __shared__ double red[RED_THREADS / 32];
-    v = warp_sum(v);
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    if (l == 0) red[w] = v;
+    __shared__ double vals[RED_THREADS];
+    vals[threadIdx.x] = v;
     __syncthreads();
     double t = 0.0;
-    if (w == 0) {
-        t = (l < RED_THREADS / 32) ? red[l] : 0.0;
+    if (threadIdx.x < 32) {
+        t = vals[threadIdx.x];
+#pragma unroll
+        for (int i = 1; i < RED_THREADS / 32; ++i) t += vals[threadIdx.x + 32 * i];
         t = warp_sum(t);
     }
     __syncthreads();
@@ -153,7 +162,7 @@ __global__ void __launch_bounds__(RED_THREADS) cg_init(int32_t n, const double* 
         st2(r, j, bv.x, bv.y);
         st2(p, j, bv.x, bv.y);
         if (p32) st2f(p32, j, bv.x, bv.y);
-        part += bv.x * bv.x + bv.y * bv.y;
+        part = fma2(part, bv.x, bv.x, bv.y, bv.y);
     }, [&](int64_t i) {
         const double bi = b[i];
         x[i] = 0.0;
@@ -192,7 +201,7 @@ __global__ void __launch_bounds__(RED_THREADS) cg_dot_pq(int32_t n, const double
         const double2 pv = ld2(p, j);
         double q0, q1;
         ld2q(q, j, q0, q1);
-        part += pv.x * q0 + pv.y * q1;
+        part = fma2(part, pv.x, q0, pv.y, q1);
     }, [&](int64_t i) { part += p[i] * as_f64(q[i]); });
     part = block_sum(part);
     if (last_block(part, partials, &st->counter)) {
@@ -226,7 +235,7 @@ __global__ void __launch_bounds__(RED_THREADS) cg_update_xr(int32_t n, double* _
         const double r0 = rv.x - alpha * q0, r1 = rv.y - alpha * q1;
         st2(x, j, xv.x + alpha * pv.x, xv.y + alpha * pv.y);
         st2(r, j, r0, r1);
-        part += r0 * r0 + r1 * r1;
+        part = fma2(part, r0, r0, r1, r1);
     }, [&](int64_t i) {
         x[i] += alpha * p[i];
         const double ri = r[i] - alpha * as_f64(q[i]);
@@ -296,7 +305,7 @@ __global__ void __launch_bounds__(RED_THREADS) cg_replace_finish(int32_t n, cons
     double part = 0.0;
     for_pairs(n, [&](int64_t j) {
         const double2 rv = ld2(r, j);
-        part += rv.x * rv.x + rv.y * rv.y;
+        part = fma2(part, rv.x, rv.x, rv.y, rv.y);
     }, [&](int64_t i) {
         const double ri = r[i];
         part += ri * ri;
@@ -350,7 +359,7 @@ __global__ void __launch_bounds__(RED_THREADS) cg_true_norm(int32_t n, const dou
     double part = 0.0;
     for_pairs(n, [&](int64_t j) {
         const double2 rv = ld2(r, j);
-        part += rv.x * rv.x + rv.y * rv.y;
+        part = fma2(part, rv.x, rv.x, rv.y, rv.y);
     }, [&](int64_t i) {
         const double ri = r[i];
         part += ri * ri;

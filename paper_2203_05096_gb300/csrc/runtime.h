@@ -52,6 +52,7 @@ struct csrk_matrix {
     int32_t* d_sr_ptr = nullptr;
     SsrDesc* d_desc = nullptr;
     int32_t* d_perm = nullptr;
+    int32_t* d_iperm = nullptr;    // inverse permutation, uploaded on the first page-locked host x
     int32_t* d_status = nullptr;
     // scratch: permuted x / y, and device copies of host vectors
     // slots: 0 permuted x, 1 permuted y, 2/3 device copies of host x/y, 4 FP32-pair split

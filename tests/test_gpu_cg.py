@@ -111,3 +111,51 @@ def test_cg_zero_rhs():
     rc, iters, rel = csrk.cg(h, bt, xt, 1e-10, 100, "f64")
     assert rc == 0 and iters == 0 and torch.all(xt == 0)
     csrk.destroy(h)
+
+
+@pytest.mark.parametrize("inner", ["f64", "f32"])
+def test_cg_kernel_choice_and_determinism(inner):
+    """The solve's SpMV on the staged kernel (0), the staged kernel with 16-bit column
+    codes (4) and the direct kernel (1): each converges to the oracle-checked residual,
+    iteration counts within 2 of each other, and each is deterministic (two solves give
+    bit-identical x)."""
+    a = synth.stencil_3d(22, 20, 18, 27, "random_dd", 11, labels=synth.vectors.permutation(22 * 20 * 18, 11))
+    b = synth.uniform_vector(a.n, 12)
+    h = setup(a)
+    bt = torch.tensor(b, device=DEV)
+    its, xs = {}, {}
+    for kernel in (0, 4, 1):
+        csrk.set_config(h, kernel=kernel, lanes=1, unroll=8, warps=16, ctas=2 if kernel != 1 else -1)
+        runs = []
+        for _ in range(2):
+            xt = torch.zeros_like(bt)
+            rc, iters, rel = csrk.cg(h, bt, xt, 1e-10, 3000, inner, 20, 0)
+            assert rc == 0 and rel <= 1e-10, (kernel, rc, iters, rel)
+            runs.append((iters, xt.cpu().numpy()))
+        assert runs[0][0] == runs[1][0] and np.array_equal(runs[0][1], runs[1][1])
+        assert true_relres(a, runs[0][1], b) <= 1.05e-10
+        its[kernel], xs[kernel] = runs[0]
+    assert abs(its[0] - its[1]) <= 2 and abs(its[4] - its[1]) <= 2, its
+    assert csrk.device_status(h) == 0
+    csrk.destroy(h)
+
+
+@pytest.mark.parametrize("kernel", [0, 1])
+def test_cg_breakdown_on_indefinite_matrix(kernel):
+    """A negative definite matrix (the negated 1-D Laplacian) gives p.q < 0 at the first
+    iteration: the solve stops with CSRK_ERR_NOT_CONVERGED, no iteration done and the
+    breakdown named, on the staged (0) and the direct (1) kernel."""
+    n = 300
+    rows, cols, vals = [], [], []
+    for i in range(n):
+        for j, v in ((i - 1, 1.0), (i, -2.0), (i + 1, 1.0)):
+            if 0 <= j < n:
+                rows.append(i); cols.append(j); vals.append(v)
+    a = synth.matrices._from_coo(n, np.array(rows), np.array(cols), np.array(vals))
+    h = setup(a, (32, 2))
+    csrk.set_config(h, kernel=kernel, lanes=1, unroll=8, warps=16, ctas=2 if kernel == 0 else -1)
+    bt = torch.tensor(synth.uniform_vector(n, 3), device=DEV)
+    rc, iters, rel = csrk.cg(h, bt, torch.zeros_like(bt), 1e-10, 100, "f64")
+    assert rc == 8 and iters == 0, (rc, iters, rel)
+    assert "breakdown" in csrk.lib().csrk_last_error().decode()
+    csrk.destroy(h)

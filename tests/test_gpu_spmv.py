@@ -321,6 +321,39 @@ def test_host_vectors():
     csrk.destroy(h)
 
 
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_host_vectors_page_locked(dtype):
+    """Page-locked host x is permuted straight from host memory (one pass, through the
+    inverse permutation): bit-identical to pageable host vectors and to device vectors,
+    for SpMV (beta = 0 and beta != 0) and for SpMM with a padded leading dimension."""
+    a = small_27pt(13)
+    x = synth.uniform_vector(a.n, 31)
+    y0 = synth.uniform_vector(a.n, 32)
+    h = make(a, 32, 4, dtype=dtype)
+    ref = gpu_spmv(h, x, 0.75, -1.5, y0)
+    assert_close(ref, a, narrowed(a, dtype), x, 0.75, -1.5, y0)
+    for beta in (0.0, -1.5):
+        want = gpu_spmv(h, x, 0.75, beta, y0)
+        yp = y0.copy()                                       # pageable host vectors
+        csrk.spmv(h, 0.75, x, beta, yp, csrk.HOST_VECTORS, stream=0)
+        xt = torch.tensor(x).pin_memory()                    # page-locked host vectors
+        yt = torch.tensor(y0).pin_memory()
+        csrk.spmv(h, 0.75, xt, beta, yt, csrk.HOST_VECTORS, stream=0)
+        assert np.array_equal(yp, want) and np.array_equal(yt.numpy(), want)
+    k, ld = 3, 4
+    X = synth.uniform_vector(a.n * ld, 33).reshape(a.n, ld)
+    Xd = torch.tensor(X, device=DEV)
+    Yd = torch.zeros((a.n, ld), dtype=torch.float64, device=DEV)
+    csrk.spmm(h, k, 1.0, Xd, ld, 0.0, Yd, ld)
+    torch.cuda.synchronize()
+    Xh = torch.tensor(X).pin_memory()
+    Yh = torch.zeros((a.n, ld), dtype=torch.float64).pin_memory()
+    csrk.spmm(h, k, 1.0, Xh, ld, 0.0, Yh, ld, csrk.HOST_VECTORS, stream=0)
+    assert np.array_equal(Yh.numpy()[:, :k], Yd.cpu().numpy()[:, :k])
+    assert csrk.device_status(h) == 0
+    csrk.destroy(h)
+
+
 # ------------------------------------------------------------------ full size
 def _full_stencil(points):
     n = 128 ** 3
