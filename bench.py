@@ -427,7 +427,13 @@ def run_ours(args, world, rank, local):
                          "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "traffic": traffic,
                          "alg_bytes_per_launch": int(abytes), "peak_kind": peak_kind,
-                         "kernel_hash": khash},
+                         "kernel_hash": khash,
+                         # the same launch against GB300's FP64 FMA rate (one FMA per nonzero):
+                         # the SpMV is co-bound by HBM and the FP64 pipe
+                         "fp64": {"achieved_gflops": round(2.0 * sd["info"]["nnz"] / (kmean * 1e-3) / 1e9, 1),
+                                  "peak_gflops": FP64_NOMINAL_GFLOPS, "peak_kind": "nominal",
+                                  "frac": round(2.0 * sd["info"]["nnz"] / (kmean * 1e-3) / 1e9
+                                                / FP64_NOMINAL_GFLOPS, 4)}},
             "e2e": e2e,
             "cg": cg,
             "batch": batch,

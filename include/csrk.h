@@ -460,6 +460,14 @@ int csrk_spmv_static_scratch(int32_t n, int32_t nssr, const int32_t* ssr_ptr,
 int csrk_selftest_bounded_wait(csrk_handle h, uint64_t timeout_ns, void* stream,
                                int32_t* status);
 
+/* csrk_selftest_narrow: check the FP64 -> FP32 narrowing the solvers use to write their
+ * FP32 copies of p (an integer rounding to nearest, ties to even: GB300 runs the
+ * conversion instruction at the slow FP64 rate).  For i < n writes by_int[i] = that
+ * narrowing of x[i] and by_cvt[i] = the conversion instruction's result; x, by_int, by_cvt
+ * are device arrays of n (not overlapping), work enqueued on `stream`.  The two agree bit
+ * for bit for every input but NaN (both NaN).  Errors: CSRK_ERR_ARG, CSRK_ERR_CUDA. */
+int csrk_selftest_narrow(const double* x, int64_t n, float* by_int, float* by_cvt, void* stream);
+
 const char* csrk_last_error(void);
 
 /* Library build description (static string): compiled architectures and options. */

@@ -1215,6 +1215,13 @@ int csrk_selftest_bounded_wait(csrk_handle h, uint64_t timeout_ns, void* stream,
     return csrk_device_status(h, stream, status);
 }
 
+int csrk_selftest_narrow(const double* x, int64_t n, float* by_int, float* by_cvt, void* stream) {
+    if (n < 0 || (n > 0 && (!x || !by_int || !by_cvt))) return fail(CSRK_ERR_ARG, "bad arguments");
+    const int e = launch_narrow_pair(x, n, by_int, by_cvt, stream);
+    if (e) return cuda_fail((cudaError_t)e, "narrowing self-test launch");
+    return CSRK_OK;
+}
+
 const char* csrk_last_error(void) { return g_last_error.c_str(); }
 
 const char* csrk_build_info(void) {

@@ -29,6 +29,7 @@
 #include <numeric>
 #include <vector>
 
+#include "convert.cuh"
 #include "kernels.cuh"
 #include "runtime.h"
 
@@ -468,7 +469,7 @@ __global__ void __launch_bounds__(VT_THREADS) bcg_init(const Chunk* __restrict__
         X[e] = 0.0;
         R[e] = b;
         P[e] = b;
-        if (P32) P32[e] = (float)b;
+        if (P32) P32[e] = csrk::dev::f64_to_f32(b);
         v += b * b;
     }
     chunk_partial(v, k, partials + (int64_t)blockIdx.x * 32);
@@ -570,7 +571,7 @@ __global__ void __launch_bounds__(VT_THREADS) bcg_update_p(const Chunk* __restri
             if (i < e1) {
                 const double pn = r[u] + beta * p[u];
                 P[i] = pn;
-                if (P32) P32[i] = (float)pn;
+                if (P32) P32[i] = csrk::dev::f64_to_f32(pn);
             }
         }
     }
@@ -593,7 +594,7 @@ __global__ void __launch_bounds__(VT_THREADS) bcg_replace(const Chunk* __restric
         if (rep) R[e] = r;
         if (rst) {
             P[e] = r;
-            if (P32) P32[e] = (float)r;
+            if (P32) P32[e] = csrk::dev::f64_to_f32(r);
         }
     }
 }

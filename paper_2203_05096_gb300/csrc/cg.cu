@@ -24,6 +24,7 @@
 #include <cstring>
 #include <new>
 
+#include "convert.cuh"
 #include "kernels.cuh"
 #include "runtime.h"
 
@@ -69,7 +70,7 @@ __device__ __forceinline__ double fma2(double part, double a, double b, double c
     return fma(c, d, fma(a, b, part));
 }
 __device__ __forceinline__ void st2f(float* p, int64_t j, double a, double b) {
-    reinterpret_cast<float2*>(p)[j] = make_float2((float)a, (float)b);
+    reinterpret_cast<float2*>(p)[j] = make_float2(csrk::dev::f64_to_f32(a), csrk::dev::f64_to_f32(b));
 }
 
 struct CgState {
@@ -168,7 +169,7 @@ __global__ void __launch_bounds__(RED_THREADS) cg_init(int32_t n, const double* 
         x[i] = 0.0;
         r[i] = bi;
         p[i] = bi;
-        if (p32) p32[i] = (float)bi;
+        if (p32) p32[i] = csrk::dev::f64_to_f32(bi);
         part += bi * bi;
     });
     part = block_sum(part);
@@ -283,7 +284,7 @@ __global__ void __launch_bounds__(RED_THREADS) cg_update_p(int32_t n, const doub
     }, [&](int64_t i) {
         const double pi = r[i] + beta * p[i];
         p[i] = pi;
-        if (p32) p32[i] = (float)pi;
+        if (p32) p32[i] = csrk::dev::f64_to_f32(pi);
     });
 }
 
@@ -344,7 +345,7 @@ __global__ void __launch_bounds__(RED_THREADS) cg_restart_p(int32_t n, const dou
     }, [&](int64_t i) {
         const double ri = r[i];
         p[i] = ri;
-        if (p32) p32[i] = (float)ri;
+        if (p32) p32[i] = csrk::dev::f64_to_f32(ri);
     });
 }
 

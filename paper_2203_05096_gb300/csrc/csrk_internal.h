@@ -157,6 +157,9 @@ int launch_gather_rows(const void* in, int64_t ldi, void* out, int64_t ldo, cons
 int launch_split_pairs(const double* in, const int32_t* perm, int32_t n, double* x64, void* pairs,
                        int32_t* flag, void* stream);
 int launch_bounded_wait_probe(unsigned long long timeout_ns, int32_t* status, void* stream);
+// by_int[i] = the solvers' integer FP64 -> FP32 narrowing of in[i], by_cvt[i] = the
+// conversion instruction's (device arrays of n)
+int launch_narrow_pair(const double* in, int64_t n, float* by_int, float* by_cvt, void* stream);
 int launch_scatter_rows(const void* in, int64_t ldi, void* out, int64_t ldo, const int32_t* perm,
                         int32_t n, int32_t k, int elem_bytes, void* stream);
 

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include "csrk_internal.h"
+#include "convert.cuh"
 #include "kernels.cuh"
 
 namespace csrk {
@@ -150,6 +151,24 @@ int launch_split_pairs(const double* in, const int32_t* perm, int32_t n, double*
     if (e != cudaSuccess) return (int)e;
     if (n == 0) return 0;
     split_pairs_kernel<<<grid_for(n), 256, 0, s>>>(in, perm, n, x64, (float2*)pairs, flag);
+    return (int)cudaGetLastError();
+}
+
+namespace {
+// both narrowings of each input: the integer one the solvers use and the instruction's
+__global__ void narrow_pair_kernel(const double* __restrict__ in, int64_t n, float* __restrict__ by_int,
+                                   float* __restrict__ by_cvt) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double d = in[i];
+        by_int[i] = dev::f64_to_f32(d);
+        by_cvt[i] = (float)d;
+    }
+}
+}  // namespace
+
+int launch_narrow_pair(const double* in, int64_t n, float* by_int, float* by_cvt, void* stream) {
+    if (n <= 0) return 0;
+    narrow_pair_kernel<<<grid_for(n), 256, 0, (cudaStream_t)stream>>>(in, n, by_int, by_cvt);
     return (int)cudaGetLastError();
 }
 

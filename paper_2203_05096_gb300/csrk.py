@@ -61,6 +61,7 @@ _PROTOS = {
     "csrk_device_status": [_vp, _vp, _pi32],
     "csrk_cg": [_vp, _vp, _vp, _d, _i32, ctypes.c_int, _i32, _i32, _u, _pi32, ctypes.POINTER(_d), _vp],
     "csrk_selftest_bounded_wait": [_vp, ctypes.c_uint64, _vp, _pi32],
+    "csrk_selftest_narrow": [_vp, _i64, _vp, _vp, _vp],
     "csrk_batch_create": [_vp, _i32, _vp, ctypes.POINTER(_vp)],
     "csrk_batch_spmm": [_vp, _d, _vp, _d, _vp, _u, _vp],
     "csrk_batch_cg": [_vp, _vp, _vp, _i32, _d, _vp, _vp, _vp],
@@ -352,6 +353,12 @@ def selftest_bounded_wait(h, timeout_ns=20_000_000, stream=None):
     st = ctypes.c_int32()
     rc = lib().csrk_selftest_bounded_wait(h, int(timeout_ns), _stream(stream), ctypes.byref(st))
     return rc, st.value
+
+
+def selftest_narrow(x, by_int, by_cvt, stream=None):
+    """Device FP64 -> FP32 narrowing of x two ways (integer rounding, conversion instruction)."""
+    _check(lib().csrk_selftest_narrow(_ptr(x), int(x.numel()), _ptr(by_int), _ptr(by_cvt),
+                                      _stream(stream, x)), "csrk_selftest_narrow")
 
 
 def build_info() -> str:
