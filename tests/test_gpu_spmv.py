@@ -73,7 +73,7 @@ def small_27pt(seed=3):
     return synth.stencil_3d(20, 17, 15, 27, "random_dd", seed, labels=synth.vectors.permutation(5100, seed))
 
 
-# ------------------------------------------------------------------ configs[0]
+# ------------------------------------------------------------------ 5-point 64x64 Laplacian, CSR-3 (32, 8)
 def test_laplacian_5pt_64x64_fp64():
     """2-D 5-point Laplacian 64x64, rows randomly permuted (seed 1) then RCM, CSR-3 with
     SR = 32 rows and SSR = 8 SRs, x ~ U[-1,1] (seed 2), y = Ax."""
