@@ -101,3 +101,10 @@ def test_empty_matrix_host_side():
     csrk.set_sizes(h, 32, 8)
     assert csrk.info(h)["nsr"] == 0 and csrk.info(h)["nssr"] == 0
     csrk.destroy(h)
+
+
+def test_selftest_narrow_arguments_checked_on_the_host():
+    lib = csrk.lib()
+    assert lib.csrk_selftest_narrow(None, -1, None, None, None) == 1     # CSRK_ERR_ARG
+    assert lib.csrk_selftest_narrow(None, 5, None, None, None) == 1      # NULL arrays for n > 0
+    assert lib.csrk_selftest_narrow(None, 0, None, None, None) == 0      # nothing to do, no launch
