@@ -605,12 +605,16 @@ int set_fixed(csrk_matrix* h, int32_t sr, int32_t ssr) {
     return CSRK_OK;
 }
 
+// The key of a tuned choice, one whitespace-free token (as the cache file stores it).
 std::string tune_key(const csrk_matrix* h) {
     cudaDeviceProp prop{};
     cudaGetDeviceProperties(&prop, h->device);
+    std::string name(prop.name);
+    for (auto& ch : name)
+        if (ch == ' ' || ch == '\t') ch = '_';
     return std::to_string(h->m.n) + ":" + std::to_string(h->m.nnz()) + ":" +
            std::to_string(h->stats.max_row_len) + ":" + std::to_string((int)h->dtype) + ":" +
-           std::to_string(h->num_sms) + ":" + std::string(prop.name) +
+           std::to_string(h->num_sms) + ":" + name +
            (h->n_long ? ":long" + std::to_string(h->n_long) : std::string());
 }
 
@@ -634,10 +638,7 @@ void save_tune_entry(const std::string& key, const TunedChoice& c) {
     if (!path) return;
     FILE* f = std::fopen(path, "a");
     if (!f) return;
-    std::string k = key;
-    for (auto& ch : k)
-        if (ch == ' ') ch = '_';
-    std::fprintf(f, "%s %d %d %d %d %d %d %d %d %.3f\n", k.c_str(), c.sr, c.ssr, c.cfg.kernel,
+    std::fprintf(f, "%s %d %d %d %d %d %d %d %d %.3f\n", key.c_str(), c.sr, c.ssr, c.cfg.kernel,
                  c.cfg.lanes, c.cfg.unroll, c.cfg.warps, c.cfg.stages, c.cfg.ctas, c.us);
     std::fclose(f);
 }

@@ -402,6 +402,41 @@ def test_autotuner_picks_a_working_config():
     csrk.destroy(h2)
 
 
+_TUNE_CHILD = '''
+import sys
+sys.path.insert(0, sys.argv[1])
+import synth
+from paper_2203_05096_gb300 import csrk
+a = synth.stencil_3d(20, 18, 16, 7, "random_dd", 3)
+h = csrk.create(a.n, a.rowptr, a.colidx, a.vals)
+csrk.reorder(h)
+csrk.set_sizes(h, 0, 0)
+inf = csrk.info(h)
+print(sorted(csrk.tuned_config(h).items()), inf["sr"], inf["ssr"])
+'''
+
+
+def test_tune_cache_file_reused_across_processes(tmp_path):
+    """CSRK_TUNE_CACHE: the first process tunes and appends one line (a whitespace-free
+    key and the choice); a second process finds it, installs the same choice and appends
+    nothing (it does not tune again)."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    cache = tmp_path / "tune.txt"
+    env = dict(os.environ, CSRK_TUNE_CACHE=str(cache))
+    runs = []
+    for _ in range(2):
+        r = subprocess.run([sys.executable, "-c", _TUNE_CHILD, root], env=env, capture_output=True, text=True,
+                           timeout=300)
+        assert r.returncode == 0, r.stderr[-2000:]
+        runs.append((r.stdout, cache.read_text().splitlines()))
+    (out1, lines1), (out2, lines2) = runs
+    assert len(lines1) == 1 and len(lines1[0].split()) == 10
+    assert lines2 == lines1 and out2 == out1
+
+
 # ------------------------------------------------------------------ FP64 on FP32 pipes
 @pytest.mark.parametrize("kernel,unroll", [(2, 4), (2, 8), (2, 16), (3, 4), (3, 8)])
 def test_pair_path_fp64_bound(kernel, unroll):
