@@ -33,7 +33,10 @@
  *     and device copies are rebuilt); csrk_reorder after the pointers exist returns
  *     CSRK_ERR_STATE.  A handle is not thread-safe: one thread uses it at a time.
  *   - Environment: CSRK_TUNE_CACHE names a file that keeps the autotuner's choices across
- *     processes; CSRK_BATCH_ITEM_BYTES overrides the batched kernel's item size;
+ *     processes (read once per process, appended to after each new tuning; one line per
+ *     choice: a whitespace-free key of the matrix shape, dtype and device, then SR, SSR,
+ *     kernel, lanes, unroll, warps, stages, blocks per SM and the measured microseconds);
+ *     CSRK_BATCH_ITEM_BYTES overrides the batched kernel's item size;
  *     CSRK_FAULT (tests) makes host-side steps fail as if their CUDA call had: "alloc"
  *     (device allocations, CSRK_ERR_ALLOC), "h2d" (matrix uploads, CSRK_ERR_CUDA), "tune"
  *     (the autotuner, CSRK_ERR_CUDA), comma-separated.
