@@ -242,3 +242,47 @@ def test_split_long_rows_arguments_and_no_long_rows():
         csrk.split_long_rows(h, 3)
     assert ei.value.status == "ERR_STATE"
     csrk.destroy(h)
+
+
+def test_property_random_csr_against_oracle():
+    """Property-based: random CSR inputs (any size up to 120, any density, columns given
+    in any order, empty rows, disconnected and nonsymmetric patterns, any SR/SSR sizes) --
+    the library's RCM permutation, B = P A P^T and pointers equal the oracle's bit for bit."""
+    hyp = pytest.importorskip("hypothesis")
+    st = pytest.importorskip("hypothesis.strategies")
+
+    @hyp.settings(max_examples=60, deadline=None, derandomize=True)
+    @hyp.given(n=st.integers(1, 120), density=st.floats(0.0, 0.25), seed=st.integers(0, 2 ** 31 - 1),
+               sr=st.integers(1, 40), ssr=st.integers(1, 9), shuffle=st.booleans())
+    def prop(n, density, seed, sr, ssr, shuffle):
+        rng = np.random.default_rng(seed)
+        mask = rng.random((n, n)) < density
+        rows, cols = np.nonzero(mask)
+        vals = rng.standard_normal(rows.size)
+        rowptr = np.zeros(n + 1, np.int64)
+        np.add.at(rowptr, rows + 1, 1)
+        rowptr = np.cumsum(rowptr)
+        colidx = cols.astype(np.int32)
+        if shuffle:                       # columns of each row in a random order
+            for i in range(n):
+                sl = slice(rowptr[i], rowptr[i + 1])
+                p = rng.permutation(rowptr[i + 1] - rowptr[i])
+                colidx[sl], vals[sl] = colidx[sl][p], vals[sl][p]
+        h = csrk.create(n, rowptr.astype(np.int32), colidx, vals)
+        perm = csrk.reorder(h, "rcm")
+        csrk.set_sizes(h, sr, ssr)
+        e = csrk.export(h)
+        # the oracle takes rows with ascending columns
+        order = np.lexsort((colidx, np.repeat(np.arange(n), np.diff(rowptr))))
+        rp = rowptr.astype(np.int32)
+        ci, vv = colidx[order], vals[order]
+        ref = reorder.rcm(n, rp, ci)
+        assert np.array_equal(perm, ref)
+        brp, bci, bv = reorder.permute_scipy(n, rp, ci, vv, ref)
+        assert np.array_equal(e["rowptr"], brp) and np.array_equal(e["colidx"], bci)
+        assert np.array_equal(e["vals"].view(np.uint64), bv.view(np.uint64))
+        srp, ssrp = ocsrk.fixed_pointers(n, sr, ssr)
+        assert np.array_equal(e["sr_ptr"], srp) and np.array_equal(e["ssr_ptr"], ssrp)
+        csrk.destroy(h)
+
+    prop()
