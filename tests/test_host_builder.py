@@ -286,3 +286,29 @@ def test_property_random_csr_against_oracle():
         csrk.destroy(h)
 
     prop()
+
+
+def test_property_bandk_random_graphs_against_oracle():
+    """Property-based: Band-k on random symmetric and nonsymmetric patterns (isolated
+    vertices, several components, any caps) -- the library equals the oracle bit for bit,
+    and every SR / SSR respects its cap."""
+    hyp = pytest.importorskip("hypothesis")
+    st = pytest.importorskip("hypothesis.strategies")
+    from oracle import bandk
+
+    @hyp.settings(max_examples=40, deadline=None, derandomize=True)
+    @hyp.given(n=st.integers(1, 90), density=st.floats(0.0, 0.12), seed=st.integers(0, 2 ** 31 - 1),
+               sr=st.integers(1, 12), ssr=st.integers(1, 6), symmetric=st.booleans())
+    def prop(n, density, seed, sr, ssr, symmetric):
+        a = synth.random_pattern(n, density, seed % 100000, symmetric=symmetric)
+        h = csrk.create(a.n, a.rowptr, a.colidx, a.vals)
+        perm = csrk.reorder_bandk(h, sr, ssr)
+        e = csrk.export(h)
+        p_ref, sr_ref, ssr_ref = bandk.bandk_py(a.n, a.rowptr, a.colidx, sr, ssr)
+        assert np.array_equal(perm, p_ref)
+        assert np.array_equal(e["sr_ptr"], sr_ref) and np.array_equal(e["ssr_ptr"], ssr_ref)
+        assert np.all(np.diff(sr_ref) >= 1) and np.all(np.diff(sr_ref) <= sr)
+        assert np.all(np.diff(ssr_ref) >= 1) and np.all(np.diff(ssr_ref) <= ssr)
+        csrk.destroy(h)
+
+    prop()
