@@ -31,6 +31,25 @@ void parallel_for(int64_t n, int64_t grain, void (*fn)(int64_t, int64_t, void*),
     for (auto& th : pool) th.join();
 }
 
+// As parallel_for, but every range except the last is a whole number of `grain` items and
+// starts at a multiple of it (callers index per-range results by start / grain).
+static void parallel_for_ranges(int64_t n, int64_t grain, void (*fn)(int64_t, int64_t, void*), void* ctx) {
+    if (n <= 0) return;
+    const int64_t blocks = (n + grain - 1) / grain;
+    unsigned hw = std::thread::hardware_concurrency();
+    const int64_t nthreads = std::max<int64_t>(1, std::min<int64_t>({(int64_t)(hw ? hw : 1), 32, blocks}));
+    if (nthreads <= 1) {
+        for (int64_t b = 0; b < n; b += grain) fn(b, std::min(n, b + grain), ctx);
+        return;
+    }
+    std::vector<std::thread> pool;
+    for (int64_t t = 0; t < nthreads; ++t)
+        pool.emplace_back([=] {
+            for (int64_t k = t; k < blocks; k += nthreads) fn(k * grain, std::min(n, (k + 1) * grain), ctx);
+        });
+    for (auto& th : pool) th.join();
+}
+
 // ---------------------------------------------------------------- ingest
 int ingest_csr(int32_t n, const int32_t* rowptr, const int32_t* colidx, const double* vals,
                CsrHost& out, std::string& err) {
@@ -92,17 +111,54 @@ struct Graph {
     int32_t deg(int32_t v) const { return (int32_t)(start[v + 1] - start[v]); }
 };
 
-bool pattern_is_symmetric(const CsrHost& a) {
-    for (int32_t i = 0; i < a.n; ++i) {
+// Rows [b, e) of the symmetry check: every off-diagonal (i, j) has its (j, i).  Threads
+// take disjoint row ranges; the answer does not depend on their number or order.
+struct SymCtx {
+    const CsrHost* a;
+    std::vector<uint8_t>* ok;   // one flag per range start
+    int64_t grain;
+};
+void sym_rows(int64_t b, int64_t e, void* vctx) {
+    const SymCtx& c = *static_cast<const SymCtx*>(vctx);
+    const CsrHost& a = *c.a;
+    bool ok = true;
+    for (int64_t i = b; i < e && ok; ++i) {
         for (int64_t p = a.rowptr[i]; p < a.rowptr[i + 1]; ++p) {
-            int32_t j = a.colidx[p];
+            const int32_t j = a.colidx[p];
             if (j == i) continue;
-            const int32_t* b = a.colidx.data() + a.rowptr[j];
-            const int32_t* e = a.colidx.data() + a.rowptr[j + 1];
-            if (!std::binary_search(b, e, i)) return false;
+            const int32_t* lo = a.colidx.data() + a.rowptr[j];
+            const int32_t* hi = a.colidx.data() + a.rowptr[j + 1];
+            if (!std::binary_search(lo, hi, (int32_t)i)) {
+                ok = false;
+                break;
+            }
         }
     }
+    if (!ok) (*c.ok)[(size_t)(b / c.grain)] = 0;
+}
+
+bool pattern_is_symmetric(const CsrHost& a) {
+    const int64_t grain = 16384;
+    std::vector<uint8_t> ok((size_t)((a.n + grain - 1) / grain) + 1, 1);
+    SymCtx ctx{&a, &ok, grain};
+    parallel_for_ranges(a.n, grain, sym_rows, &ctx);
+    for (uint8_t f : ok)
+        if (!f) return false;
     return true;
+}
+
+// Copy rows [b, e) of A's pattern without the diagonal into the neighbour lists.
+struct NbrCtx {
+    const CsrHost* a;
+    Graph* g;
+};
+void copy_nbr_rows(int64_t b, int64_t e, void* vctx) {
+    const NbrCtx& c = *static_cast<const NbrCtx*>(vctx);
+    for (int64_t i = b; i < e; ++i) {
+        int64_t w = c.g->start[i];
+        for (int64_t p = c.a->rowptr[i]; p < c.a->rowptr[i + 1]; ++p)
+            if (c.a->colidx[p] != i) c.g->nbr[w++] = c.a->colidx[p];
+    }
 }
 
 // Neighbour lists of A + A^T.  For a symmetric pattern this is A's pattern minus the
@@ -117,11 +173,8 @@ void symmetrised_graph(const CsrHost& a, Graph& g) {
             g.start[i + 1] = g.start[i] + d;
         }
         g.nbr.resize(g.start[n]);
-        for (int32_t i = 0; i < n; ++i) {
-            int64_t w = g.start[i];
-            for (int64_t p = a.rowptr[i]; p < a.rowptr[i + 1]; ++p)
-                if (a.colidx[p] != i) g.nbr[w++] = a.colidx[p];
-        }
+        NbrCtx ctx{&a, &g};
+        parallel_for_ranges(n, 16384, copy_nbr_rows, &ctx);
         return;
     }
     // General case: merge each row with the matching column of A (via the transpose).
@@ -149,9 +202,39 @@ void symmetrised_graph(const CsrHost& a, Graph& g) {
 // Breadth-first level structure from root over vertices with placed[v] == 0.  Fills
 // `order` with the reached vertices level by level; returns the level count and the
 // offset where the last level begins.
+// Large levels are expanded by several threads: each claims a vertex by swapping the tag
+// into seen_tag (exactly one thread sees the old value) and collects its finds, which are
+// appended in thread order.  The order inside a level then varies from run to run, but the
+// SET of vertices of every level does not, and the callers use only the depth and the last
+// level's set (the start search picks its least-degree, smallest-index vertex).
+struct LevelCtx {
+    const Graph* g;
+    const uint8_t* placed;
+    int32_t* seen_tag;
+    int32_t tag;
+    const int32_t* frontier;
+    std::vector<std::vector<int32_t>>* found;   // one list per range of the frontier
+    int64_t grain;
+};
+void expand_level(int64_t b, int64_t e, void* vctx) {
+    const LevelCtx& c = *static_cast<const LevelCtx*>(vctx);
+    std::vector<int32_t>& out = (*c.found)[(size_t)(b / c.grain)];
+    out.clear();
+    for (int64_t q = b; q < e; ++q) {
+        const int32_t v = c.frontier[q];
+        for (int64_t k = c.g->start[v]; k < c.g->start[v + 1]; ++k) {
+            const int32_t u = c.g->nbr[k];
+            if (c.placed[u] || __atomic_load_n(&c.seen_tag[u], __ATOMIC_RELAXED) == c.tag) continue;
+            if (__atomic_exchange_n(&c.seen_tag[u], c.tag, __ATOMIC_RELAXED) != c.tag) out.push_back(u);
+        }
+    }
+}
+
 int32_t level_structure(const Graph& g, int32_t root, const std::vector<uint8_t>& placed,
                         std::vector<int32_t>& seen_tag, int32_t tag,
                         std::vector<int32_t>& order, size_t& last_level_at) {
+    constexpr int64_t PAR_LEVEL = 8192, GRAIN = 2048;
+    std::vector<std::vector<int32_t>> found;
     order.clear();
     order.push_back(root);
     seen_tag[root] = tag;
@@ -161,6 +244,16 @@ int32_t level_structure(const Graph& g, int32_t root, const std::vector<uint8_t>
         size_t level_end = order.size();
         last_level_at = level_begin;
         ++depth;
+        const int64_t width = (int64_t)(level_end - level_begin);
+        if (width >= PAR_LEVEL) {
+            found.resize((size_t)((width + GRAIN - 1) / GRAIN));
+            LevelCtx ctx{&g, placed.data(), seen_tag.data(), tag, order.data() + level_begin, &found, GRAIN};
+            parallel_for_ranges(width, GRAIN, expand_level, &ctx);
+            for (size_t f = 0; f < (size_t)((width + GRAIN - 1) / GRAIN); ++f)
+                order.insert(order.end(), found[f].begin(), found[f].end());
+            level_begin = level_end;
+            continue;
+        }
         for (size_t q = level_begin; q < level_end; ++q) {
             int32_t v = order[q];
             for (int64_t e = g.start[v]; e < g.start[v + 1]; ++e) {

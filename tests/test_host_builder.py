@@ -312,3 +312,26 @@ def test_property_bandk_random_graphs_against_oracle():
         csrk.destroy(h)
 
     prop()
+
+
+@pytest.mark.parametrize("symmetric", [False, True])
+def test_rcm_large_random_patterns_bit_exact(symmetric):
+    """200,000 vertices, ~8 random entries per row: the start-vertex search expands its wide
+    breadth-first levels with several threads; the permutation still equals the oracle's
+    (sequential) one exactly."""
+    n = 200_000
+    rng = np.random.default_rng(3)
+    r = np.repeat(np.arange(n), rng.integers(0, 17, n))
+    c = rng.integers(0, n, r.size)
+    if symmetric:
+        r, c = np.concatenate([r, c]), np.concatenate([c, r])
+    key = np.unique(r.astype(np.int64) * n + c)
+    r, c = key // n, key % n
+    rowptr = np.zeros(n + 1, np.int64)
+    np.add.at(rowptr, r + 1, 1)
+    rowptr = np.cumsum(rowptr).astype(np.int32)
+    colidx = c.astype(np.int32)
+    h = csrk.create(n, rowptr, colidx, np.ones(colidx.size))
+    perm = csrk.reorder(h, "rcm")
+    assert np.array_equal(perm, reorder.rcm(n, rowptr, colidx))
+    csrk.destroy(h)
