@@ -16,6 +16,10 @@
  *   oracle_csr_spmv_rows  the same for a chosen subset of rows     (sampled checks at full size)
  *   oracle_csr3_spmv      the CSR-3 loop nest over super-super-rows, super-rows and rows
  *                                                                  (Listing 1, Sec. 2.2)
+ *   oracle_csr3_spmv_omp  the same loop nest with Listing 1's OpenMP parallel loop over
+ *                         super-super-rows (static schedule); CSR-2 is the case of one
+ *                         super-row per super-super-row.  The timed CPU baseline.
+ *                                                                  (Listing 1; Sec. 4.2, 6.1)
  *   oracle_csr_spmm       Y = alpha*A*X + beta*Y, k right-hand sides, X/Y row-major
  *   oracle_rcm            reverse Cuthill-McKee ordering (Sec. 2.1; reading spelled out below)
  */
@@ -75,6 +79,45 @@ void oracle_csr3_spmv(int32_t num_ssr, const int32_t* ssr_ptr, const int32_t* sr
             }
         }
     }
+}
+
+/* Listing 1 as printed, with its "parallel for" over super-super-rows: OpenMP threads
+ * share the outermost loop in equal contiguous blocks (schedule(static)).  A row's result
+ * is computed exactly as in oracle_csr3_spmv, so y is bit-identical to it for any thread
+ * count.  nthreads <= 0 uses the OpenMP default.  Returns the number of threads that ran
+ * the loop (1 when the file was built without OpenMP). */
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+int oracle_csr3_spmv_omp(int32_t num_ssr, const int32_t* ssr_ptr, const int32_t* sr_ptr,
+                         const int32_t* rowptr, const int32_t* colidx, const double* vals,
+                         const double* x, double* y, int nthreads) {
+    int used = 1;
+#ifdef _OPENMP
+    if (nthreads <= 0) nthreads = omp_get_max_threads();
+#pragma omp parallel num_threads(nthreads)
+    {
+#pragma omp single
+        used = omp_get_num_threads();
+#pragma omp for schedule(static)
+        for (int32_t i = 0; i < num_ssr; ++i) {
+            for (int32_t j = ssr_ptr[i]; j < ssr_ptr[i + 1]; ++j) {
+                for (int32_t k = sr_ptr[j]; k < sr_ptr[j + 1]; ++k) {
+                    double temp = 0.0;
+                    for (int32_t l = rowptr[k]; l < rowptr[k + 1]; ++l) {
+                        double prod = vals[l] * x[colidx[l]];
+                        temp = temp + prod;
+                    }
+                    y[k] = temp;
+                }
+            }
+        }
+    }
+#else
+    (void)nthreads;
+    oracle_csr3_spmv(num_ssr, ssr_ptr, sr_ptr, rowptr, colidx, vals, x, y);
+#endif
+    return used;
 }
 
 /* Y = alpha*A*X + beta*Y for k right-hand sides; X is n x k row-major with leading

@@ -95,6 +95,20 @@ def csr3_spmv_c(ssr_ptr, sr_ptr, rowptr, colidx, vals, x):
     return y
 
 
+def csr3_spmv_omp(ssr_ptr, sr_ptr, rowptr, colidx, vals, x, threads=0, out=None):
+    """Listing 1 with its OpenMP parallel loop over super-super-rows (static schedule), in
+    the C twin.  Returns (y, threads used); y is bit-identical to csr3_spmv_c."""
+    n = len(rowptr) - 1
+    y = np.full(n, np.nan) if out is None else out
+    used = native.lib().oracle_csr3_spmv_omp(int(len(ssr_ptr) - 1), np.ascontiguousarray(ssr_ptr, np.int32),
+                                             np.ascontiguousarray(sr_ptr, np.int32),
+                                             np.ascontiguousarray(rowptr, np.int32),
+                                             np.ascontiguousarray(colidx, np.int32),
+                                             np.ascontiguousarray(vals, np.float64),
+                                             np.ascontiguousarray(x, np.float64), y, int(threads))
+    return y, int(used)
+
+
 def csr_spmm(n, rowptr, colidx, vals, X, alpha=1.0, beta=0.0, Y=None):
     """Y = alpha*A*X + beta*Y for k right-hand sides (X, Y row-major n x k): each column
     is exactly csr_spmv of that column."""

@@ -148,3 +148,20 @@ def test_abs_scale():
     x = synth.uniform_vector(20, 20)
     s = spmv.abs_row_scale(a.rowptr, a.colidx, a.vals, x)
     assert np.allclose(s, np.abs(dense(a)) @ np.abs(x), rtol=1e-15, atol=0)
+
+
+@pytest.mark.parametrize("threads", [1, 2, 3, 8])
+@pytest.mark.parametrize("sizes", [(32, 4), (96, 1), (7, 3)])
+def test_csr3_openmp_loop_nest_matches_sequential(threads, sizes):
+    """Listing 1 with its parallel loop over super-super-rows gives the sequential loop
+    nest's y bit for bit, for any thread count and for CSR-2 (one super-row per
+    super-super-row); every row is written exactly once."""
+    from oracle import csrk as ocsrk
+    a = synth.random_pattern(3001, 0.004, 17, empty_rows=40)
+    x = synth.uniform_vector(a.n, 18)
+    sr_ptr, ssr_ptr = ocsrk.fixed_pointers(a.n, *sizes)
+    ref = spmv.csr3_spmv_c(ssr_ptr, sr_ptr, a.rowptr, a.colidx, a.vals, x)
+    got, used = spmv.csr3_spmv_omp(ssr_ptr, sr_ptr, a.rowptr, a.colidx, a.vals, x, threads)
+    assert np.array_equal(got, ref) and not np.isnan(got).any()
+    assert 1 <= used <= threads
+    assert np.array_equal(ref, spmv.csr_spmv(a.n, a.rowptr, a.colidx, a.vals, x))
