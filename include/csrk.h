@@ -387,6 +387,15 @@ int csrk_export_values(csrk_handle h, csrk_dtype dtype, void* out);
  * The library uses it only to seed its autotuner. */
 int csrk_model_sizes(double rdensity, int arch, int32_t* ssrs, int32_t* srs);
 
+/* csrk_xwin_info: the x windows of kernel 5 for the current pointers (built and uploaded
+ * on this first ask if needed, on the current device).  *available = 1 when every
+ * super-super-row's window fits the 16-bit window offsets (at most 65,536 elements), then
+ * *runs = the number of contiguous runs of x copied per SpMV over all super-super-rows
+ * (each costs one 8-byte entry of the run table, plus one sentinel entry per SSR) and
+ * *max_window = the longest window in elements (a multiple of 4).  Any output pointer may
+ * be NULL.  Errors: CSRK_ERR_ARG, CSRK_ERR_STATE (no pointers yet), CSRK_ERR_CUDA. */
+int csrk_xwin_info(csrk_handle h, int32_t* available, int64_t* runs, int32_t* max_window);
+
 /* csrk_tuned_config: the launch configuration the handle will use (any pointer may be
  * NULL):
  *   kernel   0 = TMA-staged super-super-row kernel, 1 = direct-load kernel, 2 / 3 = the
@@ -398,7 +407,24 @@ int csrk_model_sizes(double rdensity, int arch, int32_t* ssrs, int32_t* srs);
  *            are multiplied in FP64 individually.  SpMV only (SpMM uses 0 / 1);
  *            4 = TMA-staged with delta-coded 16-bit columns (csrk_index_bits = 16;
  *            lanes 1, unroll 4, 8 or 16; SpMV only, SpMM uses 0): 12 -> 10 bytes per FP64
- *            nonzero, results identical to kernel 0
+ *            nonzero, results identical to kernel 0;
+ *            5 = TMA-staged with each super-super-row's x window in shared memory: the
+ *            producer warp also copies the runs of x (aligned blocks of 4 elements) that
+ *            the SSR's columns fall in, and 16-bit column codes index that window, so the
+ *            consumers read x from shared memory instead of gathering it from L2 (10 bytes
+ *            per FP64 nonzero from HBM, results identical to kernel 0).  Available when
+ *            every SSR's window holds at most 65,536 elements and the SSRs with their
+ *            windows fit two shared-memory stages; needs a 16-byte aligned x (a tuned
+ *            kernel 5 gives way to kernel 4 or 0 for a caller's x that is not); lanes 1,
+ *            unroll 4, 8 or 16; SpMV only, SpMM uses 0;
+ *            6 = kernel 5 for FP64 handles with kernel 2's arithmetic: values stored as
+ *            (hi, lo) FP32 pairs, x split into FP32 pairs by a pass fused with its permute
+ *            (or of its own for vectors already in the reordered numbering), the windows
+ *            hold the split x and the row sums are FP32 pairs on the FP32 pipes, so a
+ *            nonzero costs no FP64 instruction (GB300 issues FP64 at about 1/64 of the
+ *            FP32 rate).  Same availability as kernels 2 and 5 together; per entry within
+ *            ~7e-13 of sum |a_ij x_j|; a launch whose x has an element outside the pair
+ *            range stages FP64 x and multiplies in FP64
  *   lanes    lanes cooperating on one row (SpMV): 1, 2, 4, 8 or 32
  *   unroll   x gathers a lane issues before consuming them; compiled (lanes, unroll)
  *            pairs: (1,4) (1,8) (1,16) (1,32) (2,8) (2,16) (4,8) (8,8) (32,4)
@@ -413,16 +439,21 @@ int csrk_tuned_config(csrk_handle h, int32_t* kernel, int32_t* lanes, int32_t* u
 
 /* csrk_set_config: force a launch configuration (same fields as csrk_tuned_config; a
  * negative field keeps the current value; a new lanes value without an unroll picks the
- * default unroll for it).  When kernel = 0 (or 2, 4) is given explicitly and the
- * super-super-rows do not fit two shared-memory stages, or kernel 2 / 4 is not available
- * for the matrix, the compute calls return CSRK_ERR_UNSUPPORTED; otherwise such a shape
- * falls back (to the direct kernel, or from 4 to 0).  Used by the autotuner and tests. */
+ * default unroll for it).  When kernel = 0 (or 2, 4, 5, 6) is given explicitly and the
+ * super-super-rows do not fit two shared-memory stages, or kernel 2 / 4 / 5 / 6 is not
+ * available for the matrix (or, for 5 and 6, the call's x is not 16-byte aligned), the
+ * compute calls return CSRK_ERR_UNSUPPORTED; otherwise such a shape falls back (to the
+ * direct kernel, from 6 to 5 or 2, from 5 to 4, from 4 to 0).  Used by the autotuner and
+ * tests. */
 int csrk_set_config(csrk_handle h, int32_t kernel, int32_t lanes, int32_t unroll,
                     int32_t warps, int32_t stages, int32_t ctas);
 
 /* csrk_device_status: synchronise the handle's work on `stream` and return the device
  * status word (0 = clean; bit 0 = a pipeline wait ran out) in *status, then clear it.
- * Returns CSRK_ERR_TIMEOUT when the word was non-zero. */
+ * Returns CSRK_ERR_TIMEOUT when the word was non-zero.  A set bit means the launches since
+ * the last check left some rows uncomputed (their results are invalid) and that a stage's
+ * copies did not complete within two bounded waits; the blocks still ended, but treat the
+ * CUDA context as suspect and re-create it before relying on later results. */
 int csrk_device_status(csrk_handle h, void* stream, int32_t* status);
 
 /* csrk_spmv_static_scratch: y = alpha*A*x + beta*y in the input numbering, for callers
@@ -435,13 +466,17 @@ int csrk_device_status(csrk_handle h, void* stream, int32_t* status);
  *   n        rows, at most 1,048,576 (larger n returns CSRK_ERR_ARG; use csrk_spmv)
  *   nssr, ssr_ptr, sr_ptr, rowptr, colidx, vals
  *            the reordered CSR-3 form in DEVICE memory, as csrk_export returns it
- *            (vals FP64; no padding needed: the kernel uses plain loads)
+ *            (vals FP64; no padding needed: the kernels use plain loads).  Rows after the
+ *            last super-row -- the long rows csrk_split_long_rows moves behind all others,
+ *            which no super-row covers -- are computed as well, one warp per row
  *   perm     DEVICE array, perm[new] = old, or NULL when there is no reordering (then the
- *            kernel works on x and y directly and the static array is not touched)
+ *            kernels work on x and y directly and the static array is not touched)
  *   x, y     DEVICE vectors of n FP64 values in the input numbering; beta = 0 makes y
- *            write-only
+ *            write-only.  With perm given x and y may be the same vector (both are copied
+ *            into the static array first); with perm NULL they must not overlap
  *   stream   cudaStream_t
- * The first call on a device looks up the static array's device address for that device
+ * The first call in a CUDA context (per device, and again after that device's context is
+ * re-created, e.g. by cudaDeviceReset) looks up the static array's device address
  * (cudaGetSymbolAddress, with that device current); make that first call before any
  * stream capture.  Every call on a device shares the one array, which keeps the last
  * call's contents; nothing in it needs clearing, because each call writes every element

@@ -50,7 +50,19 @@ bool fault_injected(const char* step) {
 NvtxRange::NvtxRange(const char* name) { nvtxRangePushA(name); }
 NvtxRange::~NvtxRange() { nvtxRangePop(); }
 
+void free_xwin(csrk_matrix* h) {
+    cudaFree(h->d_xdesc);
+    cudaFree(h->d_win);
+    cudaFree(h->d_colx);
+    h->d_xdesc = nullptr;
+    h->d_win = nullptr;
+    h->d_colx = nullptr;
+    h->xwin_ok = -1;
+    h->max_win = 0;
+}
+
 void free_ptrs(csrk_matrix* h) {
+    free_xwin(h);
     cudaFree(h->d_sr_ptr);
     cudaFree(h->d_desc);
     cudaFree(h->d_lseg);
@@ -278,6 +290,40 @@ bool col16_available(csrk_matrix* h) {
     return h->col16_ok == 1;
 }
 
+// Kernel 5's x windows (build_xwin) need every window within 65,536 elements; the
+// descriptors, runs and window codes are built and uploaded on the first ask for the
+// current pointers.
+bool xwin_available(csrk_matrix* h) {
+    if (h->xwin_ok < 0) {
+        h->xwin_ok = 0;
+        if (!h->have_ptrs || h->desc.empty()) return false;
+        NvtxRange range("csrk x windows");
+        std::vector<SsrDesc> xdesc;
+        std::vector<int32_t> win;
+        std::vector<uint16_t> colx;
+        int32_t mw = 0;
+        if (build_xwin(h->m, h->desc, xdesc, win, colx, mw) &&
+            upload_padded(&h->d_xdesc, xdesc.data(), xdesc.size(), sizeof(SsrDesc), "x-window descriptors") == CSRK_OK &&
+            upload_padded(&h->d_win, win.data(), win.size(), 4, "x-window runs") == CSRK_OK &&
+            upload_padded(&h->d_colx, colx.data(), colx.size(), 2, "x-window codes") == CSRK_OK) {
+            h->xwin_ok = 1;
+            h->max_win = mw;
+            h->xwin_runs = (int64_t)win.size() / 2 - (int64_t)xdesc.size();
+        } else {
+            cudaFree(h->d_xdesc);
+            cudaFree(h->d_win);
+            cudaFree(h->d_colx);
+            h->d_xdesc = nullptr;
+            h->d_win = nullptr;
+            h->d_colx = nullptr;
+        }
+    }
+    return h->xwin_ok == 1;
+}
+
+// (lanes, unroll) pairs compiled with x windows (kernel 5).
+bool mode4_compiled(int lanes, int unroll) { return lanes == 1 && (unroll == 4 || unroll == 8 || unroll == 16); }
+
 int smem_budget(const csrk_matrix* h, int ctas) {
     int per_cta = h->smem_per_sm / std::max(1, ctas) - 1024;
     return std::min(per_cta, h->smem_optin);
@@ -287,13 +333,16 @@ int smem_budget(const csrk_matrix* h, int ctas) {
 }  // namespace csrk
 
 bool csrk::plan_stages(const TileStats& st, int val_bytes, int max_smem, int want_stages, int col_bytes,
-                       StagePlan& plan) {
+                       StagePlan& plan, int64_t x_bytes) {
     auto r16 = [](int64_t v) { return (v + 15) & ~int64_t(15); };
     const int64_t srp = r16((int64_t)(st.max_srs + 8) * 4);
     const int64_t rp = r16((int64_t)(st.max_rows + 8) * 4);
     const int64_t col = r16((st.max_nnz + 32 / col_bytes) * col_bytes);   // slice rounded out to 16 B
     const int64_t val = r16((st.max_nnz + 16) * val_bytes);
-    int64_t stage = srp + rp + col + val;
+    const int64_t xw = r16(x_bytes);
+    // kernel 5 also stages the SSR's slice of the permutation (the fused unpermute)
+    const int64_t pm = x_bytes > 0 ? rp : 0;
+    int64_t stage = srp + rp + col + val + xw + pm;
     stage = (stage + 127) & ~int64_t(127);
     const int64_t header = 768;   // 16 stages x (2 mbarriers + one 32-byte descriptor)
     int64_t fit = (max_smem - header) / stage;
@@ -304,6 +353,8 @@ bool csrk::plan_stages(const TileStats& st, int val_bytes, int max_smem, int wan
     plan.off_rp = (uint32_t)srp;
     plan.off_col = (uint32_t)(srp + rp);
     plan.off_val = (uint32_t)(srp + rp + col);
+    plan.off_x = (uint32_t)(srp + rp + col + val);
+    plan.off_perm = (uint32_t)(srp + rp + col + val + xw);
     plan.stage_bytes = (uint32_t)stage;
     plan.header_bytes = (uint32_t)header;
     plan.stages = (int)s;
@@ -313,7 +364,7 @@ bool csrk::plan_stages(const TileStats& st, int val_bytes, int max_smem, int wan
 int csrk::launch_csr3(const LaunchArgs& a, const KernelConfig& cfg, const StagePlan& plan,
                       void* stream) {
     int e;
-    if (cfg.kernel == 2 || cfg.kernel == 3) e = launch_csr3_ds(a, cfg, plan, stream);
+    if (cfg.kernel == 2 || cfg.kernel == 3 || cfg.kernel == 6) e = launch_csr3_ds(a, cfg, plan, stream);
     else if (a.val_type == VAL_F64) e = launch_csr3_f64(a, cfg, plan, stream);
     else if (a.val_type == VAL_F32) e = launch_csr3_f32(a, cfg, plan, stream);
     else e = launch_csr3_bf16(a, cfg, plan, stream);
@@ -340,22 +391,53 @@ void fill_long_rows(const csrk_matrix* h, LaunchArgs& a, bool pairs) {
     a.lx = pairs ? static_cast<const void*>(a.x64) : a.x;
 }
 
+// The matrix arrays a launch of kernel cfg.kernel reads: the SSR descriptors, pointers and
+// column form (int32, 16-bit delta codes, or 16-bit window offsets with the windows' own
+// descriptors and runs).
+void fill_matrix_args(const csrk_matrix* h, const KernelConfig& cfg, LaunchArgs& a) {
+    a.sr_ptr = h->d_sr_ptr;
+    a.rowptr = h->d_rowptr;
+    const bool win = cfg.kernel == 5 || cfg.kernel == 6;
+    a.desc = win ? h->d_xdesc : h->d_desc;
+    a.colidx = win ? (const void*)h->d_colx : (cfg.kernel == 4 ? (const void*)h->d_col16 : (const void*)h->d_colidx);
+    a.win = win ? h->d_win : nullptr;
+}
+
 // Resolve the launch configuration and stage plan for this handle and value type.
-int resolve_config(csrk_matrix* h, int vt, KernelConfig& cfg, StagePlan& plan) {
+int resolve_config(csrk_matrix* h, int vt, KernelConfig& cfg, StagePlan& plan, int xsz, const void* x,
+                   bool spmm) {
     // the tuned / forced shape belongs to the handle's own value type; other value types
     // (the inner SpMV of a mixed-precision solve) start from the default shape
     cfg = (h->cfg_set && vt == (int)h->dtype) ? h->cfg : default_config(h);
     plan = StagePlan{};
-    const bool forced = h->kernel_forced && vt == (int)h->dtype;
+    if (spmm) {   // the pair, 16-bit-column and x-window kernels are SpMV only
+        if (cfg.kernel == 2 || cfg.kernel == 3) cfg.kernel -= 2;
+        else if (cfg.kernel >= 4) cfg.kernel = 0;   // 4, 5, 6
+    }
+    const bool forced = h->kernel_forced && vt == (int)h->dtype && !spmm;
     // other value types (a mixed solve's inner product) take the 16-bit column coding
     // whenever it fits: their bytes are mostly indices
     if (vt != (int)h->dtype && cfg.kernel == 0 && mode3_compiled(cfg.lanes, cfg.unroll) && col16_available(h))
         cfg.kernel = 4;
-    if ((cfg.kernel == 2 || cfg.kernel == 3) && (vt != VAL_F64 || !pairs_available(h))) {
+    if ((cfg.kernel == 2 || cfg.kernel == 3 || cfg.kernel == 6) && (vt != VAL_F64 || !pairs_available(h))) {
         if (forced)
             return fail(CSRK_ERR_UNSUPPORTED, "the FP32-pair FP64 path needs FP64 values in [2^-39, 2^60] "
                                               "and rows of at most 48 entries");
-        cfg.kernel -= 2;
+        cfg.kernel = cfg.kernel == 6 ? 5 : cfg.kernel - 2;
+    }
+    if (cfg.kernel == 6 && (!mode4_compiled(cfg.lanes, cfg.unroll) || !xwin_available(h) ||
+                            (x && (reinterpret_cast<uintptr_t>(x) & 15u)))) {
+        if (forced)
+            return fail(CSRK_ERR_UNSUPPORTED, "x windows need every super-super-row's window within 65,536 "
+                                              "elements, lanes 1, unroll 4, 8 or 16 and a 16-byte aligned x");
+        cfg.kernel = 2;
+    }
+    if (cfg.kernel == 5 && (!mode4_compiled(cfg.lanes, cfg.unroll) || !xwin_available(h) ||
+                            (x && (reinterpret_cast<uintptr_t>(x) & 15u)))) {
+        if (forced)
+            return fail(CSRK_ERR_UNSUPPORTED, "x windows need every super-super-row's window within 65,536 "
+                                              "elements, lanes 1, unroll 4, 8 or 16 and a 16-byte aligned x");
+        cfg.kernel = 4;
     }
     if (cfg.kernel == 4 && (!col16_available(h) || !mode3_compiled(cfg.lanes, cfg.unroll))) {
         if (forced)
@@ -366,6 +448,22 @@ int resolve_config(csrk_matrix* h, int vt, KernelConfig& cfg, StagePlan& plan) {
     }
     if ((cfg.kernel == 2 || cfg.kernel == 3) && cfg.unroll != 4 && cfg.unroll != 8 && cfg.unroll != 16)
         cfg.unroll = 8;
+    if (cfg.kernel == 5 || cfg.kernel == 6) {   // the windows must fit the stages as well
+        const int64_t xb = (int64_t)h->max_win * xsz;
+        if (cfg.ctas == 0)
+            cfg.ctas = plan_stages(h->stats, (int)val_size(vt), smem_budget(h, 2), cfg.stages, 2, plan, xb) ? 2 : 1;
+        if (plan_stages(h->stats, (int)val_size(vt), smem_budget(h, cfg.ctas), cfg.stages, 2, plan, xb))
+            return CSRK_OK;
+        if (forced)
+            return fail(CSRK_ERR_UNSUPPORTED, "super-super-rows and their x windows too large for two "
+                                              "shared-memory stages; choose smaller sizes");
+        if (cfg.kernel == 6) {
+            cfg.kernel = 2;
+        } else {
+            cfg.kernel = 4;
+            if (!col16_available(h) || !mode3_compiled(cfg.lanes, cfg.unroll)) cfg.kernel = 0;
+        }
+    }
     const bool staged = cfg.kernel == 0 || cfg.kernel == 2 || cfg.kernel == 4;
     const int cb = cfg.kernel == 4 ? 2 : 4;
     if (cfg.ctas == 0)
@@ -411,11 +509,8 @@ int compute(csrk_matrix* h, int32_t k, bool spmm, double alpha, const void* X, i
     cudaStream_t s = (cudaStream_t)stream;
     KernelConfig cfg;
     StagePlan plan;
-    if ((rc = resolve_config(h, vt, cfg, plan))) return rc;
-    // the pair and 16-bit-offset paths are SpMV only
-    if (spmm && (cfg.kernel == 2 || cfg.kernel == 3)) cfg.kernel -= 2;
-    if (spmm && cfg.kernel == 4) cfg.kernel = 0;
-    const bool pairs = cfg.kernel == 2 || cfg.kernel == 3;
+    if ((rc = resolve_config(h, vt, cfg, plan, (int)esz, nullptr, spmm))) return rc;
+    const bool pairs = cfg.kernel == 2 || cfg.kernel == 3 || cfg.kernel == 6;
     if (pairs) {
         if ((rc = ensure_vals(h, VAL_DS)) || (rc = ensure_scratch(h, 4, (size_t)n * 8)) ||
             (rc = ensure_scratch(h, 5, 16)))
@@ -479,11 +574,14 @@ int compute(csrk_matrix* h, int32_t k, bool spmm, double alpha, const void* X, i
         if (e) return cuda_fail((cudaError_t)e, "split x");
         xkern = h->d_scratch[4];
     }
+    // kernels 5 and 6 copy x by TMA (kernel 6: the FP64 x when the split flags an
+    // element): a caller's x off a 16-byte boundary takes another kernel
+    if ((cfg.kernel == 5 && (reinterpret_cast<uintptr_t>(xkern) & 15u)) ||
+        (cfg.kernel == 6 && (reinterpret_cast<uintptr_t>(xk) & 15u))) {
+        if ((rc = resolve_config(h, vt, cfg, plan, (int)esz, cfg.kernel == 6 ? xk : xkern, spmm))) return rc;
+    }
     LaunchArgs a{};
-    a.desc = h->d_desc;
-    a.sr_ptr = h->d_sr_ptr;
-    a.rowptr = h->d_rowptr;
-    a.colidx = cfg.kernel == 4 ? (const void*)h->d_col16 : (const void*)h->d_colidx;
+    fill_matrix_args(h, cfg, a);
     a.vals = h->d_vals[pairs ? (int)VAL_DS : vt];
     a.x = xkern;
     a.x64 = static_cast<const double*>(xk);
@@ -526,9 +624,9 @@ int launch_spmv_dev(csrk_matrix* h, int vt, const void* x, void* y, double alpha
     KernelConfig cfg;
     StagePlan plan;
     int rc;
-    if ((rc = resolve_config(h, vt, cfg, plan))) return rc;
+    if ((rc = resolve_config(h, vt, cfg, plan, x_f32 ? 4 : 8, x))) return rc;
     const void* xkern = x;
-    const bool pairs = cfg.kernel == 2 || cfg.kernel == 3;
+    const bool pairs = cfg.kernel == 2 || cfg.kernel == 3 || cfg.kernel == 6;
     if (pairs) {
         if ((rc = ensure_vals(h, VAL_DS)) || (rc = ensure_scratch(h, 4, (size_t)h->m.n * 8)) ||
             (rc = ensure_scratch(h, 5, 16)))
@@ -539,10 +637,7 @@ int launch_spmv_dev(csrk_matrix* h, int vt, const void* x, void* y, double alpha
         xkern = h->d_scratch[4];
     }
     LaunchArgs a{};
-    a.desc = h->d_desc;
-    a.sr_ptr = h->d_sr_ptr;
-    a.rowptr = h->d_rowptr;
-    a.colidx = cfg.kernel == 4 ? (const void*)h->d_col16 : (const void*)h->d_colidx;
+    fill_matrix_args(h, cfg, a);
     a.vals = h->d_vals[pairs ? (int)VAL_DS : vt];
     a.x = xkern;
     a.x64 = static_cast<const double*>(x);
@@ -714,6 +809,14 @@ int autotune(csrk_matrix* h) {
     h->cfg_set = false;
     h->kernel_forced = false;
     if (bandk) sizes.assign(1, {0, 0});
+    // the x-window kernel's default shape, timed beside the default shape on size pairs
+    // whose super-super-rows are small enough for its windows to fit the stages
+    KernelConfig win_cfg;
+    win_cfg.kernel = 5;
+    win_cfg.lanes = 1;
+    win_cfg.unroll = 4;
+    win_cfg.warps = 8;
+    win_cfg.ctas = 3;
     for (auto& sz : sizes) {
         if ((rc = install(sz.first, sz.second))) break;
         if ((rc = ensure_struct(h))) break;
@@ -724,8 +827,28 @@ int autotune(csrk_matrix* h) {
         StagePlan plan;
         if (resolve_config(h, vt, c.cfg, plan)) continue;   // the shape the timing ran with
         phase1.push_back(c);
+        if (!bandk && (int64_t)sz.first * sz.second > 256) continue;
+        if (rdens <= 48 && xwin_available(h)) {
+            h->cfg = win_cfg;
+            h->cfg_set = true;
+            h->kernel_forced = false;
+            TunedChoice w = c;
+            w.us = time_launches(h, s, e0, e1, reps);
+            if (resolve_config(h, vt, w.cfg, plan) == CSRK_OK && w.cfg.kernel == 5) phase1.push_back(w);
+            h->cfg_set = false;
+        }
     }
     std::sort(phase1.begin(), phase1.end(), [](auto& a, auto& b) { return a.us < b.us; });
+    // distinct size pairs in order of their best phase-1 time
+    {
+        std::vector<TunedChoice> uniq;
+        for (auto& c : phase1) {
+            bool seen = false;
+            for (auto& u : uniq) seen |= (u.sr == c.sr && u.ssr == c.ssr);
+            if (!seen) uniq.push_back(c);
+        }
+        phase1.swap(uniq);
+    }
     TunedChoice best = phase1.empty() ? TunedChoice{} : phase1.front();
 
     // lane counts for the mean row length, and -- for irregular matrices, whose longest
@@ -746,11 +869,15 @@ int autotune(csrk_matrix* h) {
         if ((rc = install(phase1[b].sr, phase1[b].ssr)) || (rc = ensure_struct(h))) break;
         for (auto& pr : pairs)
             for (int warps : {8, 16})
-                for (int kernel : {0, 1, 2, 3, 4})
-                    for (int ctas : {1, 2}) {
-                        if ((kernel == 1 || kernel == 3) && ctas == 2) continue;
+                for (int kernel : {0, 1, 2, 3, 4, 5, 6})
+                    for (int ctas : {1, 2, 3}) {
+                        if ((kernel == 1 || kernel == 3) && ctas >= 2) continue;
+                        if (ctas == 3 && (kernel < 4 || warps > 8)) continue;   // fits only small blocks
                         if ((kernel == 2 || kernel == 3) && (!with_pairs || pr.first != 1 || pr.second > 16)) continue;
                         if (kernel == 4 && (!col16_available(h) || !mode3_compiled(pr.first, pr.second))) continue;
+                        if (kernel == 5 && (!xwin_available(h) || !mode4_compiled(pr.first, pr.second))) continue;
+                        if (kernel == 6 && (!with_pairs || !xwin_available(h) || !mode4_compiled(pr.first, pr.second)))
+                            continue;
                         KernelConfig c;
                         c.kernel = kernel;
                         c.lanes = pr.first;
@@ -1000,6 +1127,18 @@ int csrk_index_bits(csrk_handle h, int32_t* bits) {
     return CSRK_OK;
 }
 
+int csrk_xwin_info(csrk_handle h, int32_t* available, int64_t* runs, int32_t* max_window) {
+    if (!h) return fail(CSRK_ERR_ARG, "handle is NULL");
+    if (!h->have_ptrs) return fail(CSRK_ERR_STATE, "call csrk_set_sizes or csrk_set_pointers first");
+    int rc;
+    if ((rc = ensure_context(h))) return rc;
+    const bool ok = xwin_available(h);
+    if (available) *available = ok ? 1 : 0;
+    if (runs) *runs = ok ? h->xwin_runs : 0;
+    if (max_window) *max_window = ok ? h->max_win : 0;
+    return CSRK_OK;
+}
+
 int csrk_set_pointers(csrk_handle h, int32_t nsr, const int32_t* sr_ptr, int32_t nssr,
                       const int32_t* ssr_ptr) {
     if (!h) return fail(CSRK_ERR_ARG, "handle is NULL");
@@ -1144,7 +1283,7 @@ int csrk_tuned_config(csrk_handle h, int32_t* kernel, int32_t* lanes, int32_t* u
         KernelConfig r;
         if (resolve_config(h, (int)h->dtype, r, plan) == CSRK_OK) {
             c = r;
-            c.stages = (c.kernel == 0 || c.kernel == 2 || c.kernel == 4) ? plan.stages : 0;
+            c.stages = (c.kernel == 0 || c.kernel == 2 || c.kernel >= 4) ? plan.stages : 0;
         }
     }
     if (kernel) *kernel = c.kernel;
@@ -1161,7 +1300,7 @@ int csrk_set_config(csrk_handle h, int32_t kernel, int32_t lanes, int32_t unroll
     if (!h) return fail(CSRK_ERR_ARG, "handle is NULL");
     KernelConfig c = h->cfg_set ? h->cfg : default_config(h);
     if (kernel >= 0) {
-        if (kernel > 4) return fail(CSRK_ERR_ARG, "kernel must be 0, 1, 2, 3 or 4");
+        if (kernel > 6) return fail(CSRK_ERR_ARG, "kernel must be 0 to 6");
         c.kernel = kernel;
         h->kernel_forced = (kernel != 1);
     }
@@ -1173,7 +1312,7 @@ int csrk_set_config(csrk_handle h, int32_t kernel, int32_t lanes, int32_t unroll
     }
     if (unroll >= 0) c.unroll = unroll;
     if (c.kernel >= 2 && (c.lanes != 1 || (c.unroll != 4 && c.unroll != 8 && c.unroll != 16)))
-        return fail(CSRK_ERR_ARG, "kernels 2, 3 and 4 take lanes 1 and unroll 4, 8 or 16");
+        return fail(CSRK_ERR_ARG, "kernels 2 to 6 take lanes 1 and unroll 4, 8 or 16");
     if (!pair_compiled(c.lanes, c.unroll))
         return fail(CSRK_ERR_ARG, "unsupported (lanes, unroll) pair; compiled: (1,4) (1,8) (1,16) "
                                   "(1,32) (2,8) (2,16) (4,8) (8,8) (32,4)");

@@ -25,8 +25,10 @@ struct alignas(16) SsrDesc {
     int32_t s0, s1;   // super-rows [s0, s1)
     int32_t r0, r1;   // rows [r0, r1)
     int32_t p0, p1;   // nonzeros [p0, p1)
-    int32_t cbase;    // smallest column of the SSR (base of its 16-bit column coding)
-    int32_t pad1;
+    int32_t cbase;    // smallest column of the SSR (base of its 16-bit column coding); in
+                      // kernel 5's copy of the descriptors: first x-window run (index into
+                      // the run array)
+    int32_t aux;      // kernel 5's copy: index of the SSR's sentinel run (one past its last)
 };
 
 struct TileStats {
@@ -56,6 +58,16 @@ bool check_pointers(int32_t n, const std::vector<int32_t>& sr_ptr,
 // Delta-coded 16-bit columns (first entry of a row from the SSR's cbase, then steps);
 // false when some code exceeds 65,535.
 bool compress_columns(const CsrHost& b, const std::vector<SsrDesc>& desc, std::vector<uint16_t>& col16);
+// x windows of kernel 5: x is staged per SSR in runs of aligned blocks of XWIN_ALIGN
+// elements (runs at most XWIN_GAP blocks apart merged).  win holds per SSR the pairs
+// (start column, offset in the window) of its runs, then a sentinel pair (elements the
+// runs cover -- the last run may end at n --, aligned window length); xdesc is desc with
+// cbase / aux = the SSR's first run / sentinel index in pairs; colx[p] = the window
+// offset of nonzero p's column.  Returns false when some window exceeds 65,536 elements.
+constexpr int32_t XWIN_ALIGN = 4;
+constexpr int32_t XWIN_GAP = 2;
+bool build_xwin(const CsrHost& b, const std::vector<SsrDesc>& desc, std::vector<SsrDesc>& xdesc,
+                std::vector<int32_t>& win, std::vector<uint16_t>& colx, int32_t& max_win);
 void build_descs(const CsrHost& b, const std::vector<int32_t>& sr_ptr,
                  const std::vector<int32_t>& ssr_ptr, std::vector<SsrDesc>& desc,
                  TileStats& st);
@@ -75,7 +87,9 @@ struct KernelConfig {
     int kernel = 0;    // 0 TMA-staged, 1 direct loads; 2 / 3 the same with FP64 values as
                        // FP32 pairs and FP32-pipe arithmetic (FP64 handles only); 4 TMA-staged
                        // with delta-coded 16-bit columns (SpMV, one row per lane, when every
-                       // code fits)
+                       // code fits); 5 TMA-staged with each SSR's x window in shared memory
+                       // and 16-bit window offsets (SpMV, one row per lane, when every window
+                       // fits)
     int lanes = 1;     // lanes per row (SpMV)
     int unroll = 8;    // x gathers issued per lane before the FMAs consume them
     int warps = 8;     // consumer warps per CTA
@@ -107,6 +121,7 @@ struct LaunchArgs {
     const int32_t* yperm; // SpMV: row r's result goes to y[yperm[r]] (fused unpermute)
     const int32_t* xflag; // pair kernels: split found an out-of-range element
     int32_t* status;
+    const int32_t* win = nullptr;   // kernel 5: x-window runs (pairs), see build_xwin
     TileStats stats;
     int val_type;       // ValType
     bool x_f32;
@@ -128,11 +143,13 @@ struct LaunchArgs {
 
 // Shared-memory plan of the TMA kernel for one value type.
 struct StagePlan {
-    uint32_t off_srp, off_rp, off_col, off_val, stage_bytes, header_bytes;
+    uint32_t off_srp, off_rp, off_col, off_val, off_x, off_perm, stage_bytes, header_bytes;
     int stages;
 };
+// x_bytes: room for the x window per stage (kernel 5, which also stages the SSR's slice of
+// the permutation; 0 otherwise).
 bool plan_stages(const TileStats& st, int val_bytes, int max_smem, int want_stages, int col_bytes,
-                 StagePlan& plan);
+                 StagePlan& plan, int64_t x_bytes = 0);
 
 // spmv_*.cu: launch on `stream`; returns a cudaError_t value (0 = success) or -1 when the
 // combination is not compiled in.

@@ -461,6 +461,93 @@ bool compress_columns(const CsrHost& b, const std::vector<SsrDesc>& desc, std::v
     return true;
 }
 
+// x windows of kernel 5.  Columns are grouped in aligned blocks of XWIN_ALIGN elements;
+// an SSR's window is the list of runs of blocks holding its columns (runs whose gap is at
+// most XWIN_GAP blocks merged), each run copied to shared memory at a running offset.
+struct XwinCtx {
+    const CsrHost* b;
+    const std::vector<SsrDesc>* desc;
+    std::vector<std::vector<int32_t>>* runs;   // per SSR: (start, base) pairs, then the sentinel pair
+    std::vector<uint16_t>* colx;
+    std::vector<uint8_t>* ok;
+};
+
+static void xwin_ssrs(int64_t t0, int64_t t1, void* vctx) {
+    auto* c = static_cast<XwinCtx*>(vctx);
+    const CsrHost& b = *c->b;
+    std::vector<int32_t> blocks;
+    for (int64_t t = t0; t < t1; ++t) {
+        const SsrDesc& d = (*c->desc)[t];
+        std::vector<int32_t>& run = (*c->runs)[t];
+        run.clear();
+        blocks.clear();
+        for (int64_t p = d.p0; p < d.p1; ++p) blocks.push_back(b.colidx[p] / XWIN_ALIGN);
+        std::sort(blocks.begin(), blocks.end());
+        blocks.erase(std::unique(blocks.begin(), blocks.end()), blocks.end());
+        // runs of blocks: [first, last] inclusive
+        int64_t base = 0;
+        size_t i = 0;
+        int32_t exact_end = 0;
+        while (i < blocks.size()) {
+            const int32_t first = blocks[i];
+            int32_t last = first;
+            while (i + 1 < blocks.size() && blocks[i + 1] - last <= XWIN_GAP + 1) last = blocks[++i];
+            ++i;
+            const int64_t start = (int64_t)first * XWIN_ALIGN;
+            const int64_t end = std::min<int64_t>((int64_t)(last + 1) * XWIN_ALIGN, b.n);
+            run.push_back((int32_t)start);
+            run.push_back((int32_t)base);
+            exact_end = (int32_t)(base + (end - start));
+            base += (int64_t)(last - first + 1) * XWIN_ALIGN;
+        }
+        run.push_back(exact_end);      // sentinel: elements the copies cover (the last run may end at n)
+        run.push_back((int32_t)std::min<int64_t>(base, INT32_MAX));   // and the aligned window length
+        if (base > 65536) {
+            (*c->ok)[t] = 0;
+            continue;
+        }
+        // window-local code of every nonzero: its run's base + offset into the run
+        const size_t nrun = run.size() / 2 - 1;
+        for (int64_t p = d.p0; p < d.p1; ++p) {
+            const int32_t col = b.colidx[p];
+            size_t lo = 0, hi = nrun;   // last run whose start <= col
+            while (hi - lo > 1) {
+                const size_t mid = (lo + hi) / 2;
+                if (run[2 * mid] <= col) lo = mid;
+                else hi = mid;
+            }
+            (*c->colx)[p] = (uint16_t)(run[2 * lo + 1] + (col - run[2 * lo]));
+        }
+    }
+}
+
+bool build_xwin(const CsrHost& b, const std::vector<SsrDesc>& desc, std::vector<SsrDesc>& xdesc,
+                std::vector<int32_t>& win, std::vector<uint16_t>& colx, int32_t& max_win) {
+    const size_t nssr = desc.size();
+    std::vector<std::vector<int32_t>> runs(nssr);
+    std::vector<uint8_t> ok(nssr, 1);
+    colx.assign(b.colidx.size(), 0);
+    XwinCtx ctx{&b, &desc, &runs, &colx, &ok};
+    parallel_for(nssr, 64, xwin_ssrs, &ctx);
+    for (uint8_t f : ok)
+        if (!f) {
+            colx.clear();
+            return false;
+        }
+    xdesc = desc;
+    win.clear();
+    max_win = 0;
+    for (size_t t = 0; t < nssr; ++t) {
+        const std::vector<int32_t>& run = runs[t];
+        const int32_t nrun = (int32_t)run.size() / 2 - 1;
+        xdesc[t].cbase = (int32_t)(win.size() / 2);
+        xdesc[t].aux = xdesc[t].cbase + nrun;
+        win.insert(win.end(), run.begin(), run.end());
+        max_win = std::max(max_win, run.back());
+    }
+    return true;
+}
+
 // ---------------------------------------------------------------- narrowing
 void narrow_f32(const double* in, float* out, int64_t n) {
     // The C conversion is IEEE round-to-nearest-even in the default rounding mode.

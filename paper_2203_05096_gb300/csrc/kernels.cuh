@@ -95,6 +95,15 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
         : "memory");
 }
 
+// As bulk_g2s, with the default L2 policy (for x, which later SSRs read again).
+__device__ __forceinline__ void bulk_g2s_keep(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
 // ------------------------------------------------------------------ value widening
 // FP32 bit pattern -> FP64 with integer instructions only (exact for every input).
 __device__ __forceinline__ double f32bits_to_f64(uint32_t u) {
@@ -243,7 +252,10 @@ __device__ __forceinline__ void store_y(XT* y, int64_t idx, AT acc, double alpha
 // a row's first entry is its column minus the SSR's cbase (folded into x by the caller),
 // every further entry the step from the previous column, so the lane rebuilds the column
 // with one integer add per nonzero.
-template <typename VT, typename XT, typename AT, int LPR, int U, typename CT = int32_t>
+// LOCAL (kernel 5): CT = uint16_t codes are offsets into the SSR's x window, which x
+// points to in shared memory (one row per lane); yperm, when set, is the SSR's staged
+// slice of the permutation, also in shared memory.
+template <typename VT, typename XT, typename AT, int LPR, int U, typename CT = int32_t, bool LOCAL = false>
 __device__ __forceinline__ void spmv_rows(int rb, int re, const int32_t* __restrict__ rp,
                                           const CT* __restrict__ col_s,
                                           const VT* __restrict__ val_s,
@@ -256,7 +268,39 @@ __device__ __forceinline__ void spmv_rows(int rb, int re, const int32_t* __restr
     for (int base = rb; base < re; base += RPP) {
         const int r = base + lane / LPR;
         AT acc = 0;
-        if constexpr (sizeof(CT) == 2) {
+        if constexpr (LOCAL) {
+            static_assert(LPR == 1 && sizeof(CT) == 2, "window codes take one row per lane");
+            if (r < re) {
+                const int pe = rp[r + 1];
+                int c = rp[r];
+                for (; c + (U - 1) < pe; c += U) {
+                    XT xv[U];
+#pragma unroll
+                    for (int t = 0; t < U; ++t) xv[t] = x[col_s[c + t]];
+#pragma unroll
+                    for (int t = 0; t < U; ++t) acc = Acc<AT>::fma(val_s[c + t], xv[t], acc);
+                }
+                // the last fewer-than-U entries in chunks of 4, 2 and 1: a warp issues an
+                // FP64 instruction only for a product some lane needs (x comes from shared
+                // memory, so the smaller chunks cost no extra memory round trips)
+                if constexpr (U > 4) {
+                    for (; c + 3 < pe; c += 4) {
+                        XT xv[4];
+#pragma unroll
+                        for (int t = 0; t < 4; ++t) xv[t] = x[col_s[c + t]];
+#pragma unroll
+                        for (int t = 0; t < 4; ++t) acc = Acc<AT>::fma(val_s[c + t], xv[t], acc);
+                    }
+                }
+                if (c + 1 < pe) {
+                    const XT x0 = x[col_s[c]], x1 = x[col_s[c + 1]];
+                    acc = Acc<AT>::fma(val_s[c], x0, acc);
+                    acc = Acc<AT>::fma(val_s[c + 1], x1, acc);
+                    c += 2;
+                }
+                if (c < pe) acc = Acc<AT>::fma(val_s[c], x[col_s[c]], acc);
+            }
+        } else if constexpr (sizeof(CT) == 2) {
             static_assert(LPR == 1, "delta-coded columns take one row per lane");
             if (r < re) {
                 const int pe = rp[r + 1];
@@ -314,7 +358,11 @@ __device__ __forceinline__ void spmv_rows(int rb, int re, const int32_t* __restr
             for (int off = LPR / 2; off > 0; off >>= 1)
                 acc += __shfl_xor_sync(0xffffffffu, acc, off);
         }
-        if (r < re && sub == 0) store_y<XT, AT>(y, yperm ? __ldg(&yperm[r]) : r, acc, alpha, beta, epi);
+        if constexpr (LOCAL) {   // the permutation slice is staged in shared memory
+            if (r < re) store_y<XT, AT>(y, yperm ? yperm[r] : r, acc, alpha, beta, epi);
+        } else {
+            if (r < re && sub == 0) store_y<XT, AT>(y, yperm ? __ldg(&yperm[r]) : r, acc, alpha, beta, epi);
+        }
     }
 }
 
@@ -367,6 +415,57 @@ __device__ __forceinline__ void spmv_rows_ds(int rb, int re, const int32_t* __re
             for (; c < pe; ++c) acc = fma(ds_value(val_s[c]), __ldg(&x64[col_s[c]]), acc);
         }
         store_y<double, double>(y, yperm ? __ldg(&yperm[r]) : r, acc, alpha, beta, epi);
+    }
+}
+
+// spmv_rows_ds over a staged x window (kernel 6): col_s are 16-bit window offsets, xs the
+// window in shared memory -- FP32 pairs of x in the fast path, FP64 x when the split pass
+// flagged an element (`slow`, uniform over the launch) -- and yperm, when set, the SSR's
+// staged slice of the permutation.
+template <int U>
+__device__ __forceinline__ void spmv_rows_ds_win(int rb, int re, const int32_t* __restrict__ rp,
+                                                 const uint16_t* __restrict__ col_s,
+                                                 const ds_t* __restrict__ val_s, const void* xs, bool slow,
+                                                 double* __restrict__ y, double alpha, double beta, int epi,
+                                                 int lane, const int32_t* __restrict__ yperm) {
+    for (int base = rb; base < re; base += 32) {
+        const int r = base + lane;
+        if (r >= re) continue;
+        const int pe = rp[r + 1];
+        int c = rp[r];
+        double acc;
+        if (!slow) {
+            const float2* __restrict__ x2 = static_cast<const float2*>(xs);
+            float sh = 0.f, sl = 0.f;
+            for (; c + U <= pe; c += U) {
+                xpair xv[U];
+#pragma unroll
+                for (int t = 0; t < U; ++t) {
+                    const float2 v = x2[col_s[c + t]];
+                    xv[t] = xpair{v.x, v.y};
+                }
+#pragma unroll
+                for (int t = 0; t < U; ++t) ds_accum(val_s[c + t], xv[t], sh, sl);
+            }
+            for (; c < pe; c += 4) {
+                xpair xv[4];
+#pragma unroll
+                for (int t = 0; t < 4; ++t)
+                    if (c + t < pe) {
+                        const float2 v = x2[col_s[c + t]];
+                        xv[t] = xpair{v.x, v.y};
+                    }
+#pragma unroll
+                for (int t = 0; t < 4; ++t)
+                    if (c + t < pe) ds_accum(val_s[c + t], xv[t], sh, sl);
+            }
+            acc = x_f64(sh) + x_f64(sl);
+        } else {
+            const double* __restrict__ x64 = static_cast<const double*>(xs);
+            acc = 0.0;
+            for (; c < pe; ++c) acc = fma(ds_value(val_s[c]), x64[col_s[c]], acc);
+        }
+        store_y<double, double>(y, yperm ? yperm[r] : r, acc, alpha, beta, epi);
     }
 }
 
@@ -454,7 +553,8 @@ struct TmaParams {
     const int32_t* yperm;  // SpMV: when set, row r's result goes to y[yperm[r]] (fused unpermute)
     const int32_t* xflag;  // MODE 2: non-zero when the split found an out-of-range element
     int32_t* status;
-    uint32_t off_srp, off_rp, off_col, off_val, stage_bytes, header_bytes;
+    const int2* win;       // MODE 4: x-window runs (start, offset) per SSR, sentinel last
+    uint32_t off_srp, off_rp, off_col, off_val, off_x, off_perm, stage_bytes, header_bytes;
     int32_t stages;
     unsigned long long timeout_ns;
 };
@@ -472,7 +572,13 @@ __device__ __forceinline__ void slice16(int64_t first, int64_t last_excl, int64_
 // lanes per row and U columns per lane.  MODE 2: SpMV with FP64 values as FP32 pairs
 // (VT = ds_t, one row per lane, FP64 accuracy on the FP32 pipes).  MODE 3: MODE 0 with
 // delta-coded 16-bit columns (2 bytes per nonzero instead of 4; see spmv_rows), one row
-// per lane, the consumers indexing x + cbase.
+// per lane, the consumers indexing x + cbase.  MODE 4 (kernel 5): the stage also holds
+// the SSR's x window -- the runs of x its columns fall in, copied by the producer warp
+// (one lane per run) -- and the 16-bit column codes are offsets into that window, so the
+// consumers read x from shared memory instead of gathering it from L2.  MODE 5 (kernel
+// 6): MODE 4 with FP64 values stored as FP32 pairs and row sums kept as FP32 pairs
+// (spmv_rows_ds_win); the window holds the split x (FP32 pairs), or FP64 x when the
+// split flagged an out-of-range element.
 // At most 60 registers per thread, so two blocks of 16 consumer warps + 1 producer warp
 // fit on one SM (65,536 registers).
 template <typename VT, typename XT, typename AT, int LPR, int MODE, int U>
@@ -496,8 +602,79 @@ __global__ void __launch_bounds__(544, 2) csr3_tma_kernel(const TmaParams P) {
     __syncthreads();
 
     if (warp == W) {
-        // ---------------- producer: one elected lane issues the bulk copies
-        if (lane == 0) {
+        constexpr int CSZ = (MODE == 3 || MODE == 4 || MODE == 5) ? 2 : 4;   // bytes per stored column
+        if constexpr (MODE == 4 || MODE == 5) {
+            // ---------------- producer warp: lane 0 copies the four slices, lane j the
+            // j-th x run of the window (32 runs per round)
+            const uint64_t pol = policy_evict_first();
+            // MODE 5 stages the FP32-pair split of x (8 bytes an element, as FP64), or the
+            // FP64 x itself when the split flagged an element
+            const XT* __restrict__ xg = static_cast<const XT*>(MODE == 5 && *P.xflag ? (const void*)P.x64 : P.x);
+            int i = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < P.nssr; t += gridDim.x, ++i) {
+                const int s = i % S;
+                const SsrDesc d = P.desc[t];
+                const int2 sent = P.win[d.aux];   // (elements covered, aligned length)
+                const int k = d.cbase + lane;
+                int2 run = make_int2(0, 0), nxt = make_int2(0, 0);
+                if (k < d.aux) {
+                    run = P.win[k];
+                    nxt = P.win[k + 1];
+                }
+                if (lane == 0 && i >= S && !mbar_wait_bounded(&empty[s], ((i / S) - 1) & 1, P.timeout_ns)) {
+                    report(P.status, 1);
+                    ok = false;
+                }
+                if (!__shfl_sync(0xffffffffu, ok, 0)) break;
+                unsigned char* st = stage0 + (size_t)s * P.stage_bytes;
+                XT* xs = reinterpret_cast<XT*>(st + P.off_x);
+                const uint32_t xexact = (uint32_t)sent.x * (uint32_t)sizeof(XT);
+                const uint32_t xbulk = xexact & ~15u;
+                if (lane == 0) {
+                    dsc[s] = d;
+                    // the window's last run may end at n off a 16-byte boundary: its last
+                    // (at most 3) elements are copied with plain loads, before the arrive
+                    if (xbulk != xexact) {
+                        const int2 lr = P.win[d.aux - 1];
+                        const int len = sent.x - lr.y;
+                        for (int e = len - (int)((xexact - xbulk) / sizeof(XT)); e < len; ++e)
+                            xs[lr.y + e] = xg[lr.x + e];
+                    }
+                    uint32_t b_srp, b_rp, b_col, b_val, b_pm = 0;
+                    int64_t o_srp, o_rp, o_col, o_val, o_pm = 0;
+                    slice16<4>(d.s0, (int64_t)d.s1 + 1, o_srp, b_srp);
+                    slice16<4>(d.r0, (int64_t)d.r1 + 1, o_rp, b_rp);
+                    slice16<CSZ>(d.p0, d.p1, o_col, b_col);
+                    slice16<sizeof(VT)>(d.p0, d.p1, o_val, b_val);
+                    if (P.yperm) slice16<4>(d.r0, d.r1, o_pm, b_pm);   // the fused unpermute's targets
+                    mbar_arrive_expect_tx(&full[s], b_srp + b_rp + b_col + b_val + xbulk + b_pm);
+                    if (b_pm) bulk_g2s(st + P.off_perm, P.yperm + o_pm, b_pm, &full[s], pol);
+                    bulk_g2s(st + P.off_srp, P.sr_ptr + o_srp, b_srp, &full[s], pol);
+                    bulk_g2s(st + P.off_rp, P.rowptr + o_rp, b_rp, &full[s], pol);
+                    if (b_col)
+                        bulk_g2s(st + P.off_col, static_cast<const unsigned char*>(P.colidx) + o_col * CSZ,
+                                 b_col, &full[s], pol);
+                    if (b_val)
+                        bulk_g2s(st + P.off_val, static_cast<const VT*>(P.vals) + o_val, b_val, &full[s], pol);
+                }
+                __syncwarp();
+                // the runs, 32 per round (after the arrive, so the expected bytes come first)
+                for (int k0 = 0; d.cbase + k0 < d.aux; k0 += 32) {
+                    const int kk = k + k0;
+                    if (kk < d.aux) {
+                        if (k0 > 0) {
+                            run = P.win[kk];
+                            nxt = P.win[kk + 1];
+                        }
+                        const int end = (kk + 1 == d.aux) ? nxt.x : nxt.y;
+                        const uint32_t b = ((uint32_t)(end - run.y) * (uint32_t)sizeof(XT)) & ~15u;
+                        if (b) bulk_g2s_keep(xs + run.y, xg + run.x, b, &full[s]);
+                    }
+                }
+            }
+        } else if (lane == 0) {
+            // ---------------- producer: one elected lane issues the bulk copies
             const uint64_t pol = policy_evict_first();
             int i = 0;
             for (int t = blockIdx.x; t < P.nssr; t += gridDim.x, ++i) {
@@ -509,15 +686,12 @@ __global__ void __launch_bounds__(544, 2) csr3_tma_kernel(const TmaParams P) {
                 const SsrDesc d = P.desc[t];
                 dsc[s] = d;
                 unsigned char* st = stage0 + (size_t)s * P.stage_bytes;
-                int64_t a0;
                 uint32_t b_srp, b_rp, b_col, b_val;
                 int64_t o_srp, o_rp, o_col, o_val;
-                constexpr int CSZ = MODE == 3 ? 2 : 4;   // bytes per stored column
                 slice16<4>(d.s0, (int64_t)d.s1 + 1, o_srp, b_srp);
                 slice16<4>(d.r0, (int64_t)d.r1 + 1, o_rp, b_rp);
                 slice16<CSZ>(d.p0, d.p1, o_col, b_col);
                 slice16<sizeof(VT)>(d.p0, d.p1, o_val, b_val);
-                (void)a0;
                 mbar_arrive_expect_tx(&full[s], b_srp + b_rp + b_col + b_val);
                 bulk_g2s(st + P.off_srp, P.sr_ptr + o_srp, b_srp, &full[s], pol);
                 bulk_g2s(st + P.off_rp, P.rowptr + o_rp, b_rp, &full[s], pol);
@@ -534,7 +708,7 @@ __global__ void __launch_bounds__(544, 2) csr3_tma_kernel(const TmaParams P) {
 
     // ---------------- consumers
     const XT* __restrict__ x = static_cast<const XT*>(P.x);
-    const bool slow = MODE == 2 && P.xflag && *P.xflag;
+    const bool slow = (MODE == 2 || MODE == 5) && P.xflag && *P.xflag;
     (void)slow;
     XT* __restrict__ y = static_cast<XT*>(P.y);
     int i = 0;
@@ -571,6 +745,15 @@ __global__ void __launch_bounds__(544, 2) csr3_tma_kernel(const TmaParams P) {
             else if constexpr (MODE == 3)
                 spmv_rows<VT, XT, AT, LPR, U, uint16_t>(rb, re, rp, col16, val, x + d.cbase, y, P.alpha,
                                                         P.beta, P.epi, lane, P.yperm);
+            else if constexpr (MODE == 5)
+                spmv_rows_ds_win<U>(rb, re, rp, col16, val, st + P.off_x, slow, y, P.alpha, P.beta, P.epi, lane,
+                                    P.yperm ? reinterpret_cast<const int32_t*>(st + P.off_perm) - (d.r0 & ~3)
+                                            : nullptr);
+            else if constexpr (MODE == 4)
+                spmv_rows<VT, XT, AT, 1, U, uint16_t, true>(
+                    rb, re, rp, col16, val, reinterpret_cast<const XT*>(st + P.off_x), y, P.alpha, P.beta,
+                    P.epi, lane,
+                    P.yperm ? reinterpret_cast<const int32_t*>(st + P.off_perm) - (d.r0 & ~3) : nullptr);
             else
                 spmm_rows<VT, XT, AT, LPR, U>(rb, re, rp, col, val, x, P.ldx, y, P.ldy, P.k,
                                                P.alpha, P.beta, P.epi, lane);

@@ -3,10 +3,36 @@
 // template instances compile in parallel.
 #pragma once
 
+#include <algorithm>
+#include <mutex>
+
 #include "kernels.cuh"
 
 namespace csrk {
 namespace dev {
+
+// Blocks of `kern` that fit on one SM at once with this block size and dynamic shared
+// memory (at least 1), remembered per (device, threads, shared memory) for each kernel.
+template <typename K>
+static int resident_blocks(K kern, int dev, int threads, int smem) {
+    struct Entry {
+        int dev, threads, smem, blocks;
+    };
+    static Entry cache[16];
+    static int used = 0;
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lock(mu);
+    for (int i = 0; i < used; ++i)
+        if (cache[i].dev == dev && cache[i].threads == threads && cache[i].smem == smem) return cache[i].blocks;
+    int blocks = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, threads, smem) != cudaSuccess) {
+        cudaGetLastError();
+        blocks = 1;
+    }
+    blocks = std::max(blocks, 1);
+    if (used < 16) cache[used++] = Entry{dev, threads, smem, blocks};
+    return blocks;
+}
 
 template <typename VT, typename XT, typename AT, int LPR, int MODE, int U>
 static int launch_one(const LaunchArgs& a, const KernelConfig& cfg, const StagePlan& plan,
@@ -31,6 +57,9 @@ static int launch_one(const LaunchArgs& a, const KernelConfig& cfg, const StageP
     P.yperm = a.yperm;
     P.xflag = a.xflag;
     P.status = a.status;
+    P.win = reinterpret_cast<const int2*>(a.win);
+    P.off_x = plan.off_x;
+    P.off_perm = plan.off_perm;
     P.off_srp = plan.off_srp;
     P.off_rp = plan.off_rp;
     P.off_col = plan.off_col;
@@ -56,10 +85,13 @@ static int launch_one(const LaunchArgs& a, const KernelConfig& cfg, const StageP
             if (dev < 64) __atomic_fetch_or(&attr_set, 1ull << dev, __ATOMIC_ACQ_REL);
         }
         const int threads = 32 * (cfg.warps + 1);
-        int grid = a.num_sms * cfg.ctas;
+        // persistent blocks: never more per SM than can be resident at once (registers,
+        // shared memory, threads), or a second partial wave would trail the first
+        const int ctas = std::min(cfg.ctas, resident_blocks(kern, dev, threads, smem));
+        int grid = a.num_sms * ctas;
         if (grid > a.nssr) grid = a.nssr;
         kern<<<grid, threads, smem, stream>>>(P);
-    } else if constexpr (MODE != 3) {   // 16-bit offsets are staged only
+    } else if constexpr (MODE != 3 && MODE != 4 && MODE != 5) {   // 16-bit codes are staged only
         auto kern = csr3_direct_kernel<VT, XT, AT, LPR, MODE, U>;
         const int threads = 32 * cfg.warps;
         int grid = a.nssr;
@@ -86,6 +118,17 @@ static int dispatch_lanes(const LaunchArgs& a, const KernelConfig& cfg, const St
             case 4: return launch_one<VT, XT, AT, 1, 3, 4>(a, c, plan, s);
             case 8: return launch_one<VT, XT, AT, 1, 3, 8>(a, c, plan, s);
             case 16: return launch_one<VT, XT, AT, 1, 3, 16>(a, c, plan, s);
+            default: return -1;
+        }
+    }
+    if (cfg.kernel == 5) {   // x windows staged in shared memory: SpMV, one row per lane
+        if (a.spmm || cfg.lanes != 1 || !a.win) return -1;
+        KernelConfig c = cfg;
+        c.kernel = 0;
+        switch (cfg.unroll) {
+            case 4: return launch_one<VT, XT, AT, 1, 4, 4>(a, c, plan, s);
+            case 8: return launch_one<VT, XT, AT, 1, 4, 8>(a, c, plan, s);
+            case 16: return launch_one<VT, XT, AT, 1, 4, 16>(a, c, plan, s);
             default: return -1;
         }
     }

@@ -47,6 +47,13 @@ struct csrk_matrix {
     int32_t* d_colidx = nullptr;
     uint16_t* d_col16 = nullptr;   // 16-bit column offsets from each SSR's cbase (kernel 4)
     int col16_ok = -1;             // offsets usable with the current pointers; -1 unknown
+    // kernel 5: per-SSR x windows (build_xwin), built and uploaded on first use
+    SsrDesc* d_xdesc = nullptr;    // descriptors with the SSR's window runs in cbase / aux
+    int32_t* d_win = nullptr;      // (start, offset) run pairs, a sentinel pair per SSR
+    uint16_t* d_colx = nullptr;    // window offset of each nonzero's column
+    int xwin_ok = -1;              // windows usable with the current pointers; -1 unknown
+    int32_t max_win = 0;           // longest window (elements, multiple of 4)
+    int64_t xwin_runs = 0;         // runs over all SSRs (sentinels not counted)
     void* d_vals[4] = {nullptr, nullptr, nullptr, nullptr};   // by ValType
     int pairs_ok = -1;             // FP32-pair path usable (values in range); -1 unknown
     int32_t* d_sr_ptr = nullptr;
@@ -90,8 +97,13 @@ int ensure_scratch(csrk_matrix* h, int slot, size_t bytes);
 KernelConfig default_config(const csrk_matrix* h);
 bool pairs_available(csrk_matrix* h);
 bool col16_available(csrk_matrix* h);
+bool xwin_available(csrk_matrix* h);
 bool mode3_compiled(int lanes, int unroll);
-int resolve_config(csrk_matrix* h, int vt, KernelConfig& cfg, StagePlan& plan);
+// xsz: bytes per x element of the launch (kernel 5 stages x); x: the launch's x, or NULL
+// when unknown (kernel 5 copies x by TMA and needs it 16-byte aligned); spmm: the launch
+// is an SpMM (kernels 2-5 are SpMV only and give way to kernel 0)
+int resolve_config(csrk_matrix* h, int vt, KernelConfig& cfg, StagePlan& plan, int xsz = 8,
+                   const void* x = nullptr, bool spmm = false);
 int compute(csrk_matrix* h, int32_t k, bool spmm, double alpha, const void* X, int64_t ldx,
             double beta, void* Y, int64_t ldy, unsigned flags, void* stream);
 // The CSR-3 kernel alone on device vectors in the reordered numbering, with value type vt;

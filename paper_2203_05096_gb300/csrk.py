@@ -71,6 +71,7 @@ _PROTOS = {
     "csrk_batch_device_status": [_vp, _pi32],
     "csrk_batch_destroy": [_vp],
     "csrk_spmv_static_scratch": [_i32, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _d, _vp, _d, _vp, _vp],
+    "csrk_xwin_info": [_vp, _vp, _vp, _vp],
 }
 
 
@@ -245,6 +246,14 @@ def tuned_config(h):
     v = [ctypes.c_int32() for _ in range(6)]
     _check(lib().csrk_tuned_config(h, *[ctypes.byref(t) for t in v]), "csrk_tuned_config")
     return dict(zip(("kernel", "lanes", "unroll", "warps", "stages", "ctas"), (t.value for t in v)))
+
+
+def xwin_info(h):
+    """Kernel 5's x windows: dict(available, runs, max_window)."""
+    av, mw = ctypes.c_int32(), ctypes.c_int32()
+    runs = ctypes.c_int64()
+    _check(lib().csrk_xwin_info(h, ctypes.byref(av), ctypes.byref(runs), ctypes.byref(mw)), "csrk_xwin_info")
+    return dict(available=bool(av.value), runs=runs.value, max_window=mw.value)
 
 
 def set_config(h, kernel=-1, lanes=-1, unroll=-1, warps=-1, stages=-1, ctas=-1):
