@@ -7,15 +7,24 @@ off-diagonals U[-1,0), int32 indices; the input rows/columns carry a random symm
 permutation (seed 3) that the CSR-k reorder (RCM) undoes; CSR-3 sizes and launch shape
 from the library's autotuner; x ~ U[-1,1] (seed 2).  Each step runs, per matrix: permute
 x into the reordered numbering, then the CSR-3 kernel storing y in the input numbering
-(fused unpermute) -- the whole device path of a natural-numbering csrk_spmv call.  Inputs are resident in HBM
-and each step's working set (~930 MB) exceeds the 129 MB L2, so no flush is needed.
+(fused unpermute) -- the whole device path of a natural-numbering csrk_spmv call.  Inputs
+are resident in HBM and each step's working set (~930 MB) exceeds the 129 MB L2, so no
+flush is needed.  Before timing, every entry of y is checked against the FP64 oracle.
 
 Metric: GFLOP/s (2 flops per stored nonzero per SpMV), whole job over all ranks.
 Roofline: HBM bytes of the dominant kernel (the 27-point CSR-3 launch) per launch over its
-mean CUDA-event duration, against the measured copy bandwidth.
+mean CUDA-event duration, against the measured copy bandwidth (and, beside it, the
+nominal 8 TB/s).
 
---impl reference times the FP64 CPU oracle (single thread, plain CSR loop) on the host
-cores on a bounded sample of the same workload.
+Also in the line (outside the timed region): the same step as 100 repeated SpMVs per
+matrix replayed from one CUDA graph; the 27-point matrix with values stored FP32 / BF16
+(FP32 or FP64 x and accumulation) with each variant's per-entry error against the FP64
+oracle; the FEM-like 160^3 matrix; CSR-2 against CSR-3 sizes on the GPU; FP64 against
+mixed-precision CG; the 64-matrix batch; and the CPU baseline: the oracle's Listing 1
+loop nest with its OpenMP parallel loop on all host cores.
+
+--impl reference times that CPU oracle (Listing 1, OpenMP, all cores) on the same
+matrices, RCM-reordered by the oracle, one SpMV of both matrices per step.
 
 Multi-GPU: replicas (one independent copy of the workload per rank, no collective on
 the data path); value = all ranks' flops / max-over-ranks time.
@@ -41,6 +50,10 @@ import synth  # noqa: E402
 SIDE = 128
 # nominal dense FP64 rate of a GB300 (152 SMs x 2 FMA/clock x 2.07 GHz x 2 flops)
 FP64_NOMINAL_GFLOPS = 1250.0
+# FP64 FMA rate measured on GB300 by a chain-of-independent-FMAs probe: 0.50-0.59 T FMA/s
+FP64_PROBE_GFLOPS = (1000.0, 1180.0)
+# nominal HBM3e bandwidth of a GB300
+NOMINAL_HBM_GBS = 8000.0
 WORKLOAD = ("128^3 7-point and 27-point random diagonally dominant stencils (FP64 values, int32 "
             "indices), rows/columns under a random symmetric permutation; y = A x per matrix per step, "
             "x and y in the input numbering")
@@ -114,17 +127,25 @@ def build_matrices(side=SIDE, only=None):
     return out
 
 
-def alg_bytes_spmv(n, nnz, nsr, nssr, val_bytes=8, x_bytes=8, fused_unpermute=True, col_bytes=4):
-    # every stored value and column index (4 bytes, or a 2-byte offset with kernel 4),
+def alg_bytes_spmv(n, nnz, nsr, nssr, val_bytes=8, x_bytes=8, fused_unpermute=True, col_bytes=4, runs=0):
+    # every stored value and column index (4 bytes, or a 2-byte code with kernels 4 and 5),
     # rowptr, sr_ptr, the 32-byte SSR descriptors, x read once and y written once
-    # (beta = 0), and the permutation read once when the kernel stores y in the input
-    # numbering
+    # (beta = 0), the permutation read once when the kernel stores y in the input
+    # numbering, and kernel 5's run table (8 bytes per run of x plus a sentinel per SSR)
     return ((val_bytes + col_bytes) * nnz + 4 * (n + 1) + 4 * (nsr + 1) + 32 * nssr + x_bytes * n + x_bytes * n
-            + (4 * n if fused_unpermute else 0))
+            + (4 * n if fused_unpermute else 0) + (8 * (runs + nssr) if runs else 0))
 
 
 def col_bytes_of(cfg):
-    return 2 if cfg.get("kernel") == 4 else 4
+    return 2 if cfg.get("kernel") in (4, 5) else 4
+
+
+def runs_of(h, cfg):
+    """Kernel 5's run count (its run table is read once per launch); 0 for other kernels."""
+    if cfg.get("kernel") != 5:
+        return 0
+    from paper_2203_05096_gb300 import csrk
+    return csrk.xwin_info(h)["runs"]
 
 
 class ClockSampler:
@@ -185,30 +206,216 @@ def visible_gpu_index(local_rank):
     return local_rank
 
 
-def cpu_oracle_gflops(mats, seconds):
-    """The FP64 oracle (plain C row loop, one thread) on whole matrices, repeated until
-    `seconds` have passed."""
+def cpu_reordered(mats):
+    """Each matrix under the oracle's own RCM ordering (B = P A P^T), the form the CPU
+    CSR-k loop nest runs on, as the GPU path does."""
+    from oracle import reorder
+    out = []
+    for name, a in mats:
+        p = reorder.rcm(a.n, a.rowptr, a.colidx)
+        rp, ci, v = reorder.permute_scipy(a.n, a.rowptr, a.colidx, a.vals, p)
+        out.append((name, a.n, rp, ci, v))
+    return out
+
+
+def cpu_listing1(rmats, sr, ssr, warm=5, runs=20, threads=0):
+    """The oracle's Listing 1 loop nest with its OpenMP parallel loop over super-super-rows
+    (static schedule) on the host cores: 5 untimed warm-ups and the mean of 20 timed runs
+    per matrix (the paper's CPU methodology, Sec. 5.4).  Returns (GFLOP/s over both
+    matrices, threads used, seconds timed)."""
+    from oracle import csrk as ocsrk
     from oracle import spmv as ospmv
-    x = {}
-    flops = 0.0
+    flops, secs, used = 0.0, 0.0, 1
+    for name, n, rp, ci, v in rmats:
+        sr_ptr, ssr_ptr = ocsrk.fixed_pointers(n, sr, ssr)
+        x = synth.uniform_vector(n, 2)
+        y = np.empty(n)
+        for _ in range(warm):
+            _, used = ospmv.csr3_spmv_omp(ssr_ptr, sr_ptr, rp, ci, v, x, threads, out=y)
+        t0 = time.perf_counter()
+        for _ in range(runs):
+            ospmv.csr3_spmv_omp(ssr_ptr, sr_ptr, rp, ci, v, x, threads, out=y)
+        secs += time.perf_counter() - t0
+        flops += runs * 2.0 * float(rp[-1])
+    return flops / secs / 1e9, used, secs
+
+
+def cpu_section(mats):
+    """CPU baseline and the host half of the CSR-2 / CSR-3 comparison (Sec. 6.1): the
+    paper's constant-time CPU choice CSR-2 with 96-row super-rows (Sec. 4.2) is the
+    baseline; a few other CSR-2 super-row sizes and CSR-3 shapes beside it, and the plain
+    single-thread CSR oracle for reference."""
+    from oracle import spmv as ospmv
     t0 = time.perf_counter()
-    reps = 0
-    while True:
-        for name, a in mats:
-            if name not in x:
-                x[name] = synth.uniform_vector(a.n, 2)
-            ospmv.csr_spmv(a.n, a.rowptr, a.colidx, a.vals, x[name])
-            flops += 2.0 * a.nnz
-        reps += 1
-        if time.perf_counter() - t0 >= seconds:
-            break
-    dt = time.perf_counter() - t0
-    return flops / dt / 1e9, f"{reps} full SpMV pass(es) over both 128^3 matrices in {dt:.1f} s"
+    rm = cpu_reordered(mats)
+    prep = time.perf_counter() - t0
+    g96, used, secs = cpu_listing1(rm, 96, 1)
+    study = {"csr2": {}, "csr3": {}}
+    for srs in (32, 384, 1536):
+        study["csr2"][str(srs)] = round(cpu_listing1(rm, srs, 1)[0], 2)
+    study["csr2"]["96"] = round(g96, 2)
+    for sr, ssr in ((32, 4), (96, 4), (32, 32)):
+        study["csr3"][f"{sr}x{ssr}"] = round(cpu_listing1(rm, sr, ssr)[0], 2)
+    # the plain single-thread oracle loop, whole matrices, two passes each
+    fl, t1 = 0.0, time.perf_counter()
+    for name, n, rp, ci, v in rm:
+        x = synth.uniform_vector(n, 2)
+        for _ in range(2):
+            ospmv.csr_spmv(n, rp, ci, v, x)
+            fl += 2.0 * float(rp[-1])
+    study["plain_csr_1_thread"] = round(fl / (time.perf_counter() - t1) / 1e9, 3)
+    study["threads"] = used
+    study["host_cores"] = os.cpu_count()
+    base = {"value": round(g96, 3), "unit": "GFLOP/s", "cores": used, "kind": "oracle",
+            "sample": f"Listing 1 loop nest (oracle C, OpenMP static over super-super-rows), CSR-2 with "
+                      f"96-row super-rows, both 128^3 matrices RCM-reordered by the oracle ({prep:.0f} s), "
+                      f"5 warm-ups + 20 timed SpMVs each ({secs:.2f} s timed)"}
+    return base, study
 
 
 # ------------------------------------------------------------------ our arm
+def max_norm_err(got, ref, s):
+    """max_i |got_i - ref_i| / s_i (rows with s_i = 0 must match exactly: inf otherwise)."""
+    err = np.abs(got - ref)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        q = np.where(s > 0, err / np.where(s > 0, s, 1.0), np.where(err > 0, np.inf, 0.0))
+    return float(np.max(q)) if q.size else 0.0
+
+
+def check_every_row(a, x, got, bound, what):
+    """Every entry of y against the FP64 oracle (Sec. 1's y = A x, Listing 1's row loop)."""
+    from oracle import spmv as ospmv
+    ref = ospmv.csr_spmv(a.n, a.rowptr, a.colidx, a.vals, x)
+    s = ospmv.abs_row_scale(a.rowptr, a.colidx, a.vals, x)
+    e = max_norm_err(got, ref, s)
+    if not e <= bound:
+        raise RuntimeError(f"{what}: result check failed before timing (max normalised error {e:.3e})")
+    return e
+
+
+def event_pair():
+    import torch
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def run_graph_100(state, stream, perm_fn, spmv_fn, XP, reps=3):
+    """The benchmark step as 100 repeated SpMVs per matrix (permute x + CSR-3 kernel),
+    recorded once into a CUDA graph and replayed; mean time per SpMV."""
+    import torch
+    out = {}
+    for s in state:
+        h = s["h"]
+        g = torch.cuda.CUDAGraph()
+        cap = torch.cuda.Stream()
+        cap.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(cap):
+            # warm the capture stream (first launches on a stream may set attributes)
+            perm_fn(h, 0, 1, s["x"].data_ptr(), 1, s["xp"].data_ptr(), 1, 0, cap.cuda_stream)
+            spmv_fn(h, 1.0, s["xp"].data_ptr(), 0.0, s["y"].data_ptr(), XP, cap.cuda_stream)
+            cap.synchronize()
+            with torch.cuda.graph(g, stream=cap):
+                rc = 0
+                for _ in range(100):
+                    rc |= perm_fn(h, 0, 1, s["x"].data_ptr(), 1, s["xp"].data_ptr(), 1, 0, cap.cuda_stream)
+                    rc |= spmv_fn(h, 1.0, s["xp"].data_ptr(), 0.0, s["y"].data_ptr(), XP, cap.cuda_stream)
+        torch.cuda.current_stream().wait_stream(cap)
+        if rc:
+            raise RuntimeError("graph capture of the SpMV loop failed")
+        g.replay()
+        torch.cuda.synchronize()
+        e0, e1 = event_pair()
+        e0.record(stream)
+        for _ in range(reps):
+            g.replay()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        us = e0.elapsed_time(e1) / (reps * 100) * 1e3
+        out[s["name"]] = {"us_per_spmv": round(us, 2), "gflops": round(2.0 * s["a"].nnz / (us * 1e-6) / 1e9, 1)}
+        del g
+    return out
+
+
+def time_kernel(h, xp, y, flags, stream, reps=50, x_f32=False):
+    """Mean CUDA-event time of the CSR-3 kernel alone (x already in the reordered numbering,
+    y stored through the permutation), in microseconds."""
+    from paper_2203_05096_gb300 import csrk
+    f = flags | (csrk.X_F32 if x_f32 else 0)
+    for _ in range(3):
+        csrk.spmv(h, 1.0, xp, 0.0, y, f)
+    import torch
+    torch.cuda.synchronize()
+    e0, e1 = event_pair()
+    e0.record(stream)
+    for _ in range(reps):
+        csrk.spmv(h, 1.0, xp, 0.0, y, f)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps * 1e3
+
+
+def run_precision(a, s64, dev, stream, peak):
+    """The 27-point matrix with values stored FP64 / FP32 / BF16 and x, accumulation in FP64
+    or FP32: kernel time, bytes and roofline fraction, and each variant's per-entry error
+    against the FP64 oracle (FP64 values, FP64 x), normalised by s_i = sum_j |a_ij x_j|."""
+    import torch
+    from oracle import spmv as ospmv
+    from paper_2203_05096_gb300 import csrk
+    x = synth.uniform_vector(a.n, 2)
+    ref = ospmv.csr_spmv(a.n, a.rowptr, a.colidx, a.vals, x)
+    sc = ospmv.abs_row_scale(a.rowptr, a.colidx, a.vals, x)
+    out = {"matrix": "stencil27", "error": "max_i |y_i - y64_i| / sum_j |a_ij x_j| against the FP64 oracle"}
+    variants = (("f64", False, False), ("f32", False, False), ("f32", True, False), ("f32", True, True),
+                ("bf16", False, False), ("bf16", True, True))
+    handles = {"f64": s64["h"]}
+    for dt, x32, acc32 in variants:
+        if dt not in handles:
+            h = csrk.create(a.n, a.rowptr, a.colidx, a.vals, dt)
+            csrk.reorder(h, "rcm", want_perm=False)
+            csrk.set_sizes(h, 0, 0)
+            handles[dt] = h
+        h = handles[dt]
+        xt = torch.tensor(x, dtype=torch.float32 if x32 else torch.float64, device=dev)
+        xp, y = torch.empty_like(xt), torch.empty_like(xt)
+        csrk.permute(h, 0, 1, xt, 1, xp, 1, csrk.X_F32 if x32 else 0)
+        fl = csrk.X_PERMUTED | (csrk.ACC_F32 if acc32 else 0)
+        us = time_kernel(h, xp, y, fl, stream, x_f32=x32)
+        got = y.double().cpu().numpy()
+        inf, cfg = csrk.info(h), csrk.tuned_config(h)
+        vb = {"f64": 8, "f32": 4, "bf16": 2}[dt]
+        ab = alg_bytes_spmv(inf["n"], inf["nnz"], inf["nsr"], inf["nssr"], vb, 4 if x32 else 8,
+                            col_bytes=col_bytes_of(cfg), runs=runs_of(h, cfg))
+        key = f"{dt}_x{'32' if x32 else '64'}_acc{'32' if acc32 else '64'}"
+        out[key] = {"kernel_us": round(us, 2), "gflops": round(2.0 * a.nnz / (us * 1e-6) / 1e9, 1),
+                    "gbs": round(ab / (us * 1e-6) / 1e9, 1), "frac_of_peak": round(ab / (us * 1e-6) / 1e9 / peak, 3),
+                    "max_err": float(f"{max_norm_err(got, ref, sc):.3e}"), "kernel": cfg["kernel"]}
+    for dt, h in handles.items():
+        if dt != "f64":
+            csrk.destroy(h)
+    return out
+
+
+def run_k_study(entries, stream):
+    """CSR-2 (one super-row per super-super-row) against CSR-3 sizes on the GPU, each size
+    pair with the matrix's tuned kernel and launch shape (Sec. 6.2 / 7): kernel time."""
+    from paper_2203_05096_gb300 import csrk
+    out = {}
+    for name, h, xp, y in entries:
+        cfg = csrk.tuned_config(h)
+        row = {}
+        for sr, ssr in ((32, 1), (64, 1), (128, 1), (32, 2), (32, 4), (32, 8)):
+            csrk.set_sizes(h, sr, ssr)
+            csrk.set_config(h, kernel=cfg["kernel"], lanes=cfg["lanes"], unroll=cfg["unroll"], warps=cfg["warps"],
+                            stages=0, ctas=0)
+            try:
+                row[f"{sr}x{ssr}"] = round(time_kernel(h, xp, y, csrk.X_PERMUTED, stream, reps=30), 1)
+            except csrk.CsrkError:
+                row[f"{sr}x{ssr}"] = None   # does not fit the forced kernel's stages
+        out[name] = row
+    return out
+
+
 def run_ours(args, world, rank, local):
-    import ctypes
+    import ctypes  # noqa: F401
 
     import torch
     from paper_2203_05096_gb300 import csrk
@@ -243,8 +450,9 @@ def run_ours(args, world, rank, local):
         inf = csrk.info(h)
         x = torch.tensor(synth.uniform_vector(a.n, 2), dtype=torch.float64, device=dev)
         xp, yp, y = torch.empty_like(x), torch.empty_like(x), torch.empty_like(x)
-        state.append(dict(name=name, a=a, h=h, info=inf, x=x, xp=xp, yp=yp, y=y,
-                          cfg=csrk.tuned_config(h), tune_s=t_tune, order_s=t_order))
+        cfg = csrk.tuned_config(h)
+        state.append(dict(name=name, a=a, h=h, info=inf, x=x, xp=xp, yp=yp, y=y, cfg=cfg,
+                          runs=runs_of(h, cfg), tune_s=t_tune, order_s=t_order))
 
     perm_fn, spmv_fn = lib.csrk_permute, lib.csrk_spmv
     XP = csrk.X_PERMUTED   # x in the reordered numbering, y stored to its input place
@@ -266,20 +474,15 @@ def run_ours(args, world, rank, local):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    # correctness guard on sampled rows before timing
-    from oracle import spmv as ospmv
+    # correctness guard before timing: every entry of y of the timed launch configuration
+    guard = {}
     for s in state:
-        rows = np.random.default_rng(1).integers(0, s["a"].n, 2000)
-        ref = ospmv.csr_spmv_rows(s["a"].rowptr, s["a"].colidx, s["a"].vals, s["x"].cpu().numpy(), rows)
-        scale = ospmv.abs_row_scale(s["a"].rowptr, s["a"].colidx, s["a"].vals, s["x"].cpu().numpy(), rows=rows)
-        got = s["y"].cpu().numpy()[rows]
         tol = 1e-12 if args.dtype == "f64" else 2.0 ** -8
-        if np.any(np.abs(got - ref) > tol * scale):
-            raise RuntimeError(f"{s['name']}: result check failed before timing")
+        guard[s["name"]] = check_every_row(s["a"], s["x"].cpu().numpy(), s["y"].cpu().numpy(), tol, s["name"])
 
     K = args.steps
     events = [[[torch.cuda.Event(enable_timing=True) for _ in range(K)] for _ in range(3)] for _ in state]
-    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_start, t_end = event_pair()
     sampler = ClockSampler(visible_gpu_index(local))
     if dist is not None:
         dist.barrier()
@@ -312,10 +515,15 @@ def run_ours(args, world, rank, local):
     # roofline of the dominant kernel: the 27-point CSR-3 launch
     peak, peak_kind = measured_peaks()
     vb = {"f64": 8, "f32": 4, "bf16": 2}[args.dtype]
+
+    def bytes_of(s):
+        inf = s["info"]
+        return alg_bytes_spmv(inf["n"], inf["nnz"], inf["nsr"], inf["nssr"], vb, col_bytes=col_bytes_of(s["cfg"]),
+                              runs=s["runs"])
+
     dom = max(range(len(state)), key=lambda j: statistics.mean(kern_ms[j]))
     sd = state[dom]
-    inf = sd["info"]
-    abytes = alg_bytes_spmv(inf["n"], inf["nnz"], inf["nsr"], inf["nssr"], vb, col_bytes=col_bytes_of(sd["cfg"]))
+    abytes = bytes_of(sd)
     kmean = statistics.mean(kern_ms[dom])
     achieved = abytes / (kmean * 1e-3) / 1e9
     khash = kernel_source_hash()
@@ -324,18 +532,18 @@ def run_ours(args, world, rank, local):
 
     per_matrix = {}
     for j, s in enumerate(state):
-        inf = s["info"]
         km = statistics.mean(kern_ms[j])
-        b = alg_bytes_spmv(inf["n"], inf["nnz"], inf["nsr"], inf["nssr"], vb, col_bytes=col_bytes_of(s["cfg"]))
-        per_matrix[s["name"]] = {"n": inf["n"], "nnz": inf["nnz"], "kernel_us": round(km * 1e3, 2),
-                                 "kernel_min_us": round(min(kern_ms[j]) * 1e3, 2),
-                                 "kernel_gflops": round(2.0 * inf["nnz"] / (km * 1e-3) / 1e9, 1),
-                                 "kernel_gbs": round(b / (km * 1e-3) / 1e9, 1),
-                                 "kernel_frac_of_peak": round(b / (km * 1e-3) / 1e9 / peak, 3),
+        b = bytes_of(s)
+        gbs = b / (km * 1e-3) / 1e9
+        c = s["cfg"]
+        per_matrix[s["name"]] = {"kernel_us": round(km * 1e3, 2), "kernel_min_us": round(min(kern_ms[j]) * 1e3, 2),
+                                 "gbs": round(gbs, 1), "frac_of_peak": round(gbs / peak, 3),
+                                 "frac_of_nominal": round(gbs / NOMINAL_HBM_GBS, 3),
+                                 "gflops": round(2.0 * s["info"]["nnz"] / (km * 1e-3) / 1e9, 1),
                                  "permute_us": round(statistics.mean(perm_ms[j]) * 1e3, 2),
-                                 "sr": inf["sr"], "ssr": inf["ssr"], "nsr": inf["nsr"], "nssr": inf["nssr"],
-                                 "config": s["cfg"],
-                                 "setup_s": round(s["tune_s"], 2), "order_s": round(s["order_s"], 2)}
+                                 "alg_bytes": int(b), "sizes": [s["info"]["sr"], s["info"]["ssr"]],
+                                 "shape": f"k{c['kernel']} u{c['unroll']} w{c['warps']} s{c['stages']} c{c['ctas']}",
+                                 "max_err": float(f"{guard[s['name']]:.2e}")}
 
     # end to end: the public call with host vectors (pinned), copies inside the timed region
     e2e = None
@@ -354,7 +562,7 @@ def run_ours(args, world, rank, local):
         torch.cuda.synchronize()
         if dist is not None:
             dist.barrier()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0, e1 = event_pair()
         e0.record(stream)
         for _ in range(E):
             e2e_step()
@@ -365,10 +573,14 @@ def run_ours(args, world, rank, local):
                "h2d_bytes_per_step": int(sum(8 * s["a"].n for s in state)),
                "d2h_bytes_per_step": int(sum(8 * s["a"].n for s in state))}
 
+    graph = None
+    if not args.no_graph:
+        graph = run_graph_100(state, stream, perm_fn, spmv_fn, XP)
+
     # conjugate gradients to rtol 1e-10 on the 27-point matrix: FP64 against mixed precision
     cg = None
-    if not args.no_cg:
-        s27 = state[-1]
+    s27 = next((s for s in state if s["name"] == "stencil27"), None)
+    if not args.no_cg and s27 is not None:
         b = torch.tensor(synth.uniform_vector(s27["a"].n, 5), dtype=torch.float64, device=dev)
         xs = torch.empty_like(b)
         cg = {"matrix": s27["name"], "rtol": 1e-10, "replace_every": 20, "runs": {}}
@@ -377,7 +589,7 @@ def run_ours(args, world, rank, local):
             torch.cuda.synchronize()
             times = []
             for rep in range(3):
-                c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                c0, c1 = event_pair()
                 c0.record(stream)
                 if rep == 0:
                     torch.cuda.nvtx.range_push(f"cg_{inner}")   # lets a profiler keep one solve
@@ -394,14 +606,30 @@ def run_ours(args, world, rank, local):
         for k in ("f32", "bf16"):
             cg["runs"][k]["speedup_vs_f64"] = round(f64 / cg["runs"][k]["ms"], 3)
 
+    precision = None
+    if not args.no_precision and s27 is not None and args.dtype == "f64":
+        precision = run_precision(s27["a"], s27, dev, stream, peak)
+
+    fem, fem_entry = None, None
+    if not args.no_fem and args.side == SIDE:
+        fem, fem_entry = run_fem(args, dev, keep=True)
+
+    k_study = None
+    if not args.no_kstudy:
+        entries = [(s["name"], s["h"], s["xp"], s["y"]) for s in state]
+        if fem_entry is not None:
+            entries.append(fem_entry)
+        k_study = run_k_study(entries, stream)
+    if fem_entry is not None:
+        csrk.destroy(fem_entry[1])
+
     batch = None
     if not args.no_batch:
         batch = run_batch(args, dev, stream, peak)
 
-    cpu = None
+    cpu, cpu_study = None, None
     if rank == 0 and world == 1 and not args.no_cpu:
-        g, sample = cpu_oracle_gflops(mats, args.cpu_seconds)
-        cpu = {"value": round(g, 3), "unit": "GFLOP/s", "cores": 1, "kind": "oracle", "sample": sample}
+        cpu, cpu_study = cpu_section(mats)
 
     if rank == 0:
         line = {
@@ -417,30 +645,35 @@ def run_ours(args, world, rank, local):
             "vs_baseline": None,
             "dtype": args.dtype,
             "data": "synthetic",
-            "config": {"workload": WORKLOAD,
-                       "method": "CSR-3 sizes and launch shape from the library autotuner; per matrix "
-                                 "permute x, then the CSR-3 kernel storing y in the input numbering",
+            "config": {"workload": "128^3 7-pt + 27-pt stencils, FP64, int32, random labels undone by RCM",
+                       "l2": "inputs larger than L2 (~930 MB per step vs 129 MB), no flush",
                        "sizes": args.sizes, "ordering": args.ordering if args.ordering == "rcm" else
-                       f"bandk {args.bandk_caps}", "l2": "inputs larger than L2 (~930 MB per step vs 129 MB)",
-                       "parallelism": f"replicas x{world}", "per_matrix": per_matrix},
-            "roofline": {"bound": "hbm", "kernel": f"csr3 {state[dom]['name']}",
+                       f"bandk {args.bandk_caps}", "parallelism": f"replicas x{world}"},
+            "roofline": {"bound": "hbm", "kernel": f"csr3 {sd['name']}",
                          "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "traffic": traffic,
                          "alg_bytes_per_launch": int(abytes), "peak_kind": peak_kind,
+                         "nominal_gbs": NOMINAL_HBM_GBS, "frac_of_nominal": round(achieved / NOMINAL_HBM_GBS, 4),
                          "kernel_hash": khash,
                          # the same launch against GB300's FP64 FMA rate (one FMA per nonzero):
                          # the SpMV is co-bound by HBM and the FP64 pipe
                          "fp64": {"achieved_gflops": round(2.0 * sd["info"]["nnz"] / (kmean * 1e-3) / 1e9, 1),
-                                  "peak_gflops": FP64_NOMINAL_GFLOPS, "peak_kind": "nominal",
-                                  "frac": round(2.0 * sd["info"]["nnz"] / (kmean * 1e-3) / 1e9
-                                                / FP64_NOMINAL_GFLOPS, 4)}},
+                                  "nominal_gflops": FP64_NOMINAL_GFLOPS, "probe_gflops": list(FP64_PROBE_GFLOPS),
+                                  "frac_of_nominal": round(2.0 * sd["info"]["nnz"] / (kmean * 1e-3) / 1e9
+                                                           / FP64_NOMINAL_GFLOPS, 4)}},
             "e2e": e2e,
-            "cg": cg,
             "batch": batch,
+            "cg": cg,
+            "wall_s_timed": round(wall, 3),
             "gpu_launches": K * 2 * len(state),   # per matrix: permute x, CSR-3 kernel (+ fused unpermute)
             "clocks": clocks,
+            "per_matrix": per_matrix,
+            "graph_100": graph,
+            "precision": precision,
+            "fem": fem,
+            "k_study_gpu_us": k_study,
+            "cpu_study_gflops": cpu_study,
             "cpu_baseline": cpu,
-            "wall_s_timed": round(wall, 3),
         }
         print(json.dumps(line), flush=True)
     for s in state:
@@ -595,17 +828,19 @@ def run_irregular(args, dev):
     return out
 
 
-def run_fem(args, dev):
+def run_fem(args, dev, keep=False):
     """The FEM-like SPD matrix on 160^3 jittered points (n = 4,096,000, ~61 M nonzeros,
     12-18 neighbours per row, random labels): natural-numbering SpMV (permute x, CSR-3
-    kernel with the fused unpermute), autotuned, kernel time with CUDA events and the same
-    algorithmic-byte roofline as the stencils."""
+    kernel with the fused unpermute), autotuned; kernel time with CUDA events, the same
+    algorithmic-byte roofline as the stencils, and every entry of y against the FP64
+    oracle.  With keep, also returns (name, handle, x_p, y) for the size study."""
     import torch
     from paper_2203_05096_gb300 import csrk
     t0 = time.perf_counter()
     a = synth.fem_like(160, 4)
     gen_s = time.perf_counter() - t0
-    x = torch.tensor(synth.uniform_vector(a.n, 2), dtype=torch.float64, device=dev)
+    xh = synth.uniform_vector(a.n, 2)
+    x = torch.tensor(xh, dtype=torch.float64, device=dev)
     y = torch.empty_like(x)
     stream = torch.cuda.current_stream(dev)
     h = csrk.create(a.n, a.rowptr, a.colidx, a.vals)
@@ -614,8 +849,9 @@ def run_fem(args, dev):
     for _ in range(5):
         csrk.spmv(h, 1.0, x, 0.0, y)
     torch.cuda.synchronize()
+    err = check_every_row(a, xh, y.cpu().numpy(), 1e-12, "FEM 160^3")
     reps = max(20, args.steps)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0, e1 = event_pair()
     e0.record(stream)
     for _ in range(reps):
         csrk.spmv(h, 1.0, x, 0.0, y)
@@ -627,52 +863,48 @@ def run_fem(args, dev):
     # kernel alone (x already permuted; y stored through the permutation)
     xp = torch.empty_like(x)
     csrk.permute(h, 0, 1, x, 1, xp, 1)
-    e0.record(stream)
-    for _ in range(reps):
-        csrk.spmv(h, 1.0, xp, 0.0, y, csrk.X_PERMUTED)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    kus = e0.elapsed_time(e1) / reps * 1e3
-    ab = alg_bytes_spmv(inf["n"], inf["nnz"], inf["nsr"], inf["nssr"], 8, col_bytes=col_bytes_of(cfg))
-    out = {"workload": "FEM-like SPD, 160^3 jittered points, 12-18 neighbours per row, random labels, FP64",
-           "n": int(a.n), "nnz": int(a.nnz), "generate_s": round(gen_s, 1), "config": cfg,
-           "sr": inf["sr"], "ssr": inf["ssr"], "call_us": round(us, 2),
-           "call_gflops": round(2.0 * a.nnz / (us * 1e-6) / 1e9, 1), "kernel_us": round(kus, 2),
-           "kernel_gflops": round(2.0 * a.nnz / (kus * 1e-6) / 1e9, 1),
+    kus = time_kernel(h, xp, y, csrk.X_PERMUTED, stream, reps=reps)
+    ab = alg_bytes_spmv(inf["n"], inf["nnz"], inf["nsr"], inf["nssr"], 8, col_bytes=col_bytes_of(cfg),
+                        runs=runs_of(h, cfg))
+    out = {"n": int(a.n), "nnz": int(a.nnz), "generate_s": round(gen_s, 1),
+           "sizes": [inf["sr"], inf["ssr"]],
+           "shape": f"k{cfg['kernel']} u{cfg['unroll']} w{cfg['warps']} s{cfg['stages']} c{cfg['ctas']}",
+           "call_us": round(us, 2), "call_gflops": round(2.0 * a.nnz / (us * 1e-6) / 1e9, 1),
+           "kernel_us": round(kus, 2), "kernel_gflops": round(2.0 * a.nnz / (kus * 1e-6) / 1e9, 1),
            "kernel_alg_bytes": int(ab), "kernel_gbs": round(ab / (kus * 1e-6) / 1e9, 1),
-           "kernel_frac_of_peak": round(ab / (kus * 1e-6) / 1e9 / peak, 3), "peak_kind": peak_kind}
+           "kernel_frac_of_peak": round(ab / (kus * 1e-6) / 1e9 / peak, 3), "max_err": float(f"{err:.2e}")}
+    if keep:
+        return out, ("fem160", h, xp, y)
     csrk.destroy(h)
     return out
 
 
 # ------------------------------------------------------------------ reference arm
 def run_reference(args, world, rank, local):
-    """The FP64 CPU oracle as it stands, on the host cores, each step a bounded block of
-    rows of both matrices (rotating through the matrix)."""
+    """The FP64 CPU oracle as it stands: Listing 1's loop nest with its OpenMP parallel loop
+    over super-super-rows, on all host cores, over both matrices RCM-reordered by the
+    oracle; CSR-2 with 96-row super-rows (Sec. 4.2's constant-time CPU choice).  One step =
+    one SpMV of each matrix (the whole workload)."""
     if rank != 0:
         return
+    from oracle import csrk as ocsrk
     from oracle import spmv as ospmv
     mats = build_matrices(args.side, args.only)
-    xs = [synth.uniform_vector(a.n, 2) for _, a in mats]
-    budget = max(0.005, min(0.5, 60.0 / max(1, args.steps + args.warmup)))
-    # calibrate rows per block on the densest matrix
-    a27 = mats[-1][1]
-    probe = np.arange(0, 20000, dtype=np.int64)
     t0 = time.perf_counter()
-    ospmv.csr_spmv_rows(a27.rowptr, a27.colidx, a27.vals, xs[1], probe)
-    per_row = (time.perf_counter() - t0) / probe.size
-    rows_per_block = max(1000, int(budget / 2 / max(per_row, 1e-9)))
-    cursor = [0, 0]
+    rm = cpu_reordered(mats)
+    prep = time.perf_counter() - t0
+    work = []
+    for name, n, rp, ci, v in rm:
+        sr_ptr, ssr_ptr = ocsrk.fixed_pointers(n, 96, 1)
+        work.append((sr_ptr, ssr_ptr, rp, ci, v, synth.uniform_vector(n, 2), np.empty(n)))
+    used = 1
 
     def step():
+        nonlocal used
         fl = 0.0
-        for j, (_, a) in enumerate(mats):
-            b = cursor[j]
-            e = min(a.n, b + rows_per_block)
-            rows = np.arange(b, e, dtype=np.int64)
-            ospmv.csr_spmv_rows(a.rowptr, a.colidx, a.vals, xs[j], rows)
-            fl += 2.0 * float(a.rowptr[e] - a.rowptr[b])
-            cursor[j] = 0 if e >= a.n else e
+        for sr_ptr, ssr_ptr, rp, ci, v, x, y in work:
+            _, used = ospmv.csr3_spmv_omp(ssr_ptr, sr_ptr, rp, ci, v, x, 0, out=y)
+            fl += 2.0 * float(rp[-1])
         return fl
 
     for _ in range(args.warmup):
@@ -683,7 +915,8 @@ def run_reference(args, world, rank, local):
         flops += step()
     dt = time.perf_counter() - t0
     value = flops / dt / 1e9
-    sample = f"{rows_per_block} rows of each matrix per step, {args.steps} steps, {dt:.1f} s"
+    sample = (f"every row of both 128^3 matrices per step (RCM by the oracle, {prep:.0f} s before timing), "
+              f"Listing 1 loop nest, CSR-2 with 96-row super-rows, OpenMP static, {args.steps} steps in {dt:.2f} s")
     line = {
         "impl": "reference",
         "metric": "SpMV GFLOP/s (CSR-3, 128^3 7-point + 27-point stencils, FP64)",
@@ -691,9 +924,9 @@ def run_reference(args, world, rank, local):
         "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD,
-                   "method": "FP64 CPU oracle: plain CSR loop over the matrices in the input numbering"},
-        "cpu_baseline": {"value": round(value, 3), "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+        "config": {"workload": "128^3 7-pt + 27-pt stencils, FP64, int32, random labels undone by RCM",
+                   "method": "FP64 CPU oracle: Listing 1 loop nest with OpenMP over super-super-rows"},
+        "cpu_baseline": {"value": round(value, 3), "unit": "GFLOP/s", "cores": used, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": round(value, 3), "unit": "GFLOP/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
@@ -710,11 +943,16 @@ def main():
     p.add_argument("--dtype", choices=("f64", "f32", "bf16"), default="f64")
     p.add_argument("--config", default="", help="force a launch config, e.g. kernel=0,lanes=1,warps=8")
     p.add_argument("--sizes", default="auto", help="'auto' (autotuner) or 'sr,ssr'")
-    p.add_argument("--cpu-seconds", type=float, default=10.0)
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cg", action="store_true")
     p.add_argument("--no-batch", action="store_true")
+    p.add_argument("--no-graph", action="store_true", help="skip the 100-SpMV CUDA-graph replay")
+    p.add_argument("--no-precision", action="store_true", help="skip the FP32/BF16-value variants")
+    p.add_argument("--no-fem", action="store_true", help="skip the FEM 160^3 matrix")
+    p.add_argument("--no-kstudy", action="store_true", help="skip the CSR-2 / CSR-3 size study")
+    p.add_argument("--quick", action="store_true",
+                   help="headline step only (no e2e, graph, CG, precision, FEM, size study, batch, CPU)")
     p.add_argument("--side", type=int, default=SIDE, help="grid side (profiling runs use a smaller case)")
     p.add_argument("--only", choices=[m for m, _ in MATRICES], default=None)
     p.add_argument("--ordering", choices=("rcm", "bandk"), default="rcm",
@@ -729,6 +967,9 @@ def main():
     args = p.parse_args()
     if args.warmup < 3:
         p.error("--warmup must be >= 3")
+    if args.quick:
+        args.no_e2e = args.no_graph = args.no_cg = args.no_precision = args.no_fem = True
+        args.no_kstudy = args.no_batch = args.no_cpu = True
     world, rank, local = dist_env()
     if args.irregular:
         import torch
