@@ -127,25 +127,29 @@ def build_matrices(side=SIDE, only=None):
     return out
 
 
-def alg_bytes_spmv(n, nnz, nsr, nssr, val_bytes=8, x_bytes=8, fused_unpermute=True, col_bytes=4, runs=0):
-    # every stored value and column index (4 bytes, or a 2-byte code with kernels 4 and 5),
+def alg_bytes_spmv(n, nnz, nsr, nssr, val_bytes=8, x_bytes=8, fused_unpermute=True, col_bytes=4, runs=0,
+                   row_order=False):
+    # every stored value and column index (4 bytes, or a 2-byte code with kernels 4 to 6),
     # rowptr, sr_ptr, the 32-byte SSR descriptors, x read once and y written once
     # (beta = 0), the permutation read once when the kernel stores y in the input
-    # numbering, and kernel 5's run table (8 bytes per run of x plus a sentinel per SSR)
+    # numbering, and for kernels 5 / 6 the run table (8 bytes per run of x, a 4-byte run
+    # pointer per SSR) and the rows' length order when it is used (2 bytes per row)
     return ((val_bytes + col_bytes) * nnz + 4 * (n + 1) + 4 * (nsr + 1) + 32 * nssr + x_bytes * n + x_bytes * n
-            + (4 * n if fused_unpermute else 0) + (8 * (runs + nssr) if runs else 0))
+            + (4 * n if fused_unpermute else 0) + (8 * runs + 4 * (nssr + 1) if runs else 0)
+            + (2 * n if row_order else 0))
 
 
 def col_bytes_of(cfg):
-    return 2 if cfg.get("kernel") in (4, 5) else 4
+    return 2 if cfg.get("kernel") in (4, 5, 6) else 4
 
 
-def runs_of(h, cfg):
-    """Kernel 5's run count (its run table is read once per launch); 0 for other kernels."""
-    if cfg.get("kernel") != 5:
-        return 0
+def window_of(h, cfg):
+    """Kernels 5 / 6: (run count, whether the row length order is used); (0, False) otherwise."""
+    if cfg.get("kernel") not in (5, 6):
+        return 0, False
     from paper_2203_05096_gb300 import csrk
-    return csrk.xwin_info(h)["runs"]
+    w = csrk.xwin_info(h)
+    return w["runs"], w["row_order"]
 
 
 class ClockSampler:
@@ -382,8 +386,9 @@ def run_precision(a, s64, dev, stream, peak):
         got = y.double().cpu().numpy()
         inf, cfg = csrk.info(h), csrk.tuned_config(h)
         vb = {"f64": 8, "f32": 4, "bf16": 2}[dt]
+        runs, ro = window_of(h, cfg)
         ab = alg_bytes_spmv(inf["n"], inf["nnz"], inf["nsr"], inf["nssr"], vb, 4 if x32 else 8,
-                            col_bytes=col_bytes_of(cfg), runs=runs_of(h, cfg))
+                            col_bytes=col_bytes_of(cfg), runs=runs, row_order=ro)
         key = f"{dt}_x{'32' if x32 else '64'}_acc{'32' if acc32 else '64'}"
         out[key] = {"kernel_us": round(us, 2), "gflops": round(2.0 * a.nnz / (us * 1e-6) / 1e9, 1),
                     "gbs": round(ab / (us * 1e-6) / 1e9, 1), "frac_of_peak": round(ab / (us * 1e-6) / 1e9 / peak, 3),
@@ -451,8 +456,9 @@ def run_ours(args, world, rank, local):
         x = torch.tensor(synth.uniform_vector(a.n, 2), dtype=torch.float64, device=dev)
         xp, yp, y = torch.empty_like(x), torch.empty_like(x), torch.empty_like(x)
         cfg = csrk.tuned_config(h)
+        runs, ro = window_of(h, cfg)
         state.append(dict(name=name, a=a, h=h, info=inf, x=x, xp=xp, yp=yp, y=y, cfg=cfg,
-                          runs=runs_of(h, cfg), tune_s=t_tune, order_s=t_order))
+                          runs=runs, row_order=ro, tune_s=t_tune, order_s=t_order))
 
     perm_fn, spmv_fn = lib.csrk_permute, lib.csrk_spmv
     XP = csrk.X_PERMUTED   # x in the reordered numbering, y stored to its input place
@@ -519,7 +525,7 @@ def run_ours(args, world, rank, local):
     def bytes_of(s):
         inf = s["info"]
         return alg_bytes_spmv(inf["n"], inf["nnz"], inf["nsr"], inf["nssr"], vb, col_bytes=col_bytes_of(s["cfg"]),
-                              runs=s["runs"])
+                              runs=s["runs"], row_order=s["row_order"])
 
     dom = max(range(len(state)), key=lambda j: statistics.mean(kern_ms[j]))
     sd = state[dom]
@@ -542,6 +548,7 @@ def run_ours(args, world, rank, local):
                                  "gflops": round(2.0 * s["info"]["nnz"] / (km * 1e-3) / 1e9, 1),
                                  "permute_us": round(statistics.mean(perm_ms[j]) * 1e3, 2),
                                  "alg_bytes": int(b), "sizes": [s["info"]["sr"], s["info"]["ssr"]],
+                                 "x_runs": int(s["runs"]),
                                  "shape": f"k{c['kernel']} u{c['unroll']} w{c['warps']} s{c['stages']} c{c['ctas']}",
                                  "max_err": float(f"{guard[s['name']]:.2e}")}
 
@@ -864,8 +871,9 @@ def run_fem(args, dev, keep=False):
     xp = torch.empty_like(x)
     csrk.permute(h, 0, 1, x, 1, xp, 1)
     kus = time_kernel(h, xp, y, csrk.X_PERMUTED, stream, reps=reps)
-    ab = alg_bytes_spmv(inf["n"], inf["nnz"], inf["nsr"], inf["nssr"], 8, col_bytes=col_bytes_of(cfg),
-                        runs=runs_of(h, cfg))
+    runs, ro = window_of(h, cfg)
+    ab = alg_bytes_spmv(inf["n"], inf["nnz"], inf["nsr"], inf["nssr"], 8, col_bytes=col_bytes_of(cfg), runs=runs,
+                        row_order=ro)
     out = {"n": int(a.n), "nnz": int(a.nnz), "generate_s": round(gen_s, 1),
            "sizes": [inf["sr"], inf["ssr"]],
            "shape": f"k{cfg['kernel']} u{cfg['unroll']} w{cfg['warps']} s{cfg['stages']} c{cfg['ctas']}",

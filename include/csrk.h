@@ -387,14 +387,18 @@ int csrk_export_values(csrk_handle h, csrk_dtype dtype, void* out);
  * The library uses it only to seed its autotuner. */
 int csrk_model_sizes(double rdensity, int arch, int32_t* ssrs, int32_t* srs);
 
-/* csrk_xwin_info: the x windows of kernel 5 for the current pointers (built and uploaded
- * on this first ask if needed, on the current device).  *available = 1 when every
- * super-super-row's window fits the 16-bit window offsets (at most 65,536 elements), then
- * *runs = the number of contiguous runs of x copied per SpMV over all super-super-rows
- * (each costs one 8-byte entry of the run table, plus one sentinel entry per SSR) and
- * *max_window = the longest window in elements (a multiple of 4).  Any output pointer may
- * be NULL.  Errors: CSRK_ERR_ARG, CSRK_ERR_STATE (no pointers yet), CSRK_ERR_CUDA. */
-int csrk_xwin_info(csrk_handle h, int32_t* available, int64_t* runs, int32_t* max_window);
+/* csrk_xwin_info: the x windows of kernels 5 and 6 for the current pointers (built and
+ * uploaded on this first ask if needed, on the current device).  *available = 1 when
+ * every super-super-row's window fits the 16-bit window offsets (at most 65,536
+ * elements), then *runs = the number of contiguous runs of x copied per SpMV over all
+ * super-super-rows (each costs one 8-byte entry of the run table), *max_window = the
+ * longest window in elements (a multiple of 4) and *row_order = 1 when the kernels hand
+ * each super-super-row's rows to warp passes in order of length (built when that saves at
+ * least 5 % of the passes' FP64 instruction slots: rows of unequal length; 2 bytes per row
+ * more per SpMV).  Any output pointer may be NULL.  Errors: CSRK_ERR_ARG, CSRK_ERR_STATE
+ * (no pointers yet), CSRK_ERR_CUDA. */
+int csrk_xwin_info(csrk_handle h, int32_t* available, int64_t* runs, int32_t* max_window,
+                   int32_t* row_order);
 
 /* csrk_tuned_config: the launch configuration the handle will use (any pointer may be
  * NULL):
@@ -449,7 +453,9 @@ int csrk_set_config(csrk_handle h, int32_t kernel, int32_t lanes, int32_t unroll
                     int32_t warps, int32_t stages, int32_t ctas);
 
 /* csrk_device_status: synchronise the handle's work on `stream` and return the device
- * status word (0 = clean; bit 0 = a pipeline wait ran out) in *status, then clear it.
+ * status word (0 = clean; bit 0 = a pipeline wait ran out; bit 1 = in a bounds-checked
+ * build, libcsrk_checks.so, a CSR-3 kernel met an index outside its array and skipped that
+ * super-row or super-super-row) in *status, then clear it.
  * Returns CSRK_ERR_TIMEOUT when the word was non-zero.  A set bit means the launches since
  * the last check left some rows uncomputed (their results are invalid) and that a stage's
  * copies did not complete within two bounded waits; the blocks still ended, but treat the

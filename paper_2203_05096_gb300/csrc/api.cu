@@ -53,10 +53,14 @@ NvtxRange::~NvtxRange() { nvtxRangePop(); }
 void free_xwin(csrk_matrix* h) {
     cudaFree(h->d_xdesc);
     cudaFree(h->d_win);
+    cudaFree(h->d_wptr);
     cudaFree(h->d_colx);
+    cudaFree(h->d_rord);
     h->d_xdesc = nullptr;
     h->d_win = nullptr;
+    h->d_wptr = nullptr;
     h->d_colx = nullptr;
+    h->d_rord = nullptr;
     h->xwin_ok = -1;
     h->max_win = 0;
 }
@@ -299,23 +303,28 @@ bool xwin_available(csrk_matrix* h) {
         if (!h->have_ptrs || h->desc.empty()) return false;
         NvtxRange range("csrk x windows");
         std::vector<SsrDesc> xdesc;
-        std::vector<int32_t> win;
+        std::vector<int32_t> win, wptr;
         std::vector<uint16_t> colx;
         int32_t mw = 0;
-        if (build_xwin(h->m, h->desc, xdesc, win, colx, mw) &&
+        int64_t runs = 0;
+        if (build_xwin(h->m, h->desc, xdesc, win, wptr, colx, mw, runs) &&
             upload_padded(&h->d_xdesc, xdesc.data(), xdesc.size(), sizeof(SsrDesc), "x-window descriptors") == CSRK_OK &&
             upload_padded(&h->d_win, win.data(), win.size(), 4, "x-window runs") == CSRK_OK &&
+            upload_padded(&h->d_wptr, wptr.data(), wptr.size(), 4, "x-window run pointers") == CSRK_OK &&
             upload_padded(&h->d_colx, colx.data(), colx.size(), 2, "x-window codes") == CSRK_OK) {
             h->xwin_ok = 1;
             h->max_win = mw;
-            h->xwin_runs = (int64_t)win.size() / 2 - (int64_t)xdesc.size();
+            h->xwin_runs = runs;
+            // rows of unequal length: hand them to warp passes in length order when that
+            // saves at least 5 % of the passes' FP64 issue slots
+            std::vector<uint16_t> ord;
+            int64_t nat = 0, srt = 0;
+            build_row_order(h->m, h->sr_ptr, h->desc, ord, nat, srt);
+            if (srt < nat - nat / 20 && upload_padded(&h->d_rord, ord.data(), ord.size(), 2, "row order") != CSRK_OK)
+                h->d_rord = nullptr;   // the natural order still works
         } else {
-            cudaFree(h->d_xdesc);
-            cudaFree(h->d_win);
-            cudaFree(h->d_colx);
-            h->d_xdesc = nullptr;
-            h->d_win = nullptr;
-            h->d_colx = nullptr;
+            free_xwin(h);
+            h->xwin_ok = 0;
         }
     }
     return h->xwin_ok == 1;
@@ -342,7 +351,9 @@ bool csrk::plan_stages(const TileStats& st, int val_bytes, int max_smem, int wan
     const int64_t xw = r16(x_bytes);
     // kernel 5 also stages the SSR's slice of the permutation (the fused unpermute)
     const int64_t pm = x_bytes > 0 ? rp : 0;
-    int64_t stage = srp + rp + col + val + xw + pm;
+    // ... and, for irregular rows, the SSR's slice of the rows' length order
+    const int64_t od = x_bytes > 0 ? r16((int64_t)(st.max_rows + 16) * 2) : 0;
+    int64_t stage = srp + rp + col + val + xw + pm + od;
     stage = (stage + 127) & ~int64_t(127);
     const int64_t header = 768;   // 16 stages x (2 mbarriers + one 32-byte descriptor)
     int64_t fit = (max_smem - header) / stage;
@@ -355,6 +366,7 @@ bool csrk::plan_stages(const TileStats& st, int val_bytes, int max_smem, int wan
     plan.off_val = (uint32_t)(srp + rp + col);
     plan.off_x = (uint32_t)(srp + rp + col + val);
     plan.off_perm = (uint32_t)(srp + rp + col + val + xw);
+    plan.off_ord = (uint32_t)(srp + rp + col + val + xw + pm);
     plan.stage_bytes = (uint32_t)stage;
     plan.header_bytes = (uint32_t)header;
     plan.stages = (int)s;
@@ -401,6 +413,11 @@ void fill_matrix_args(const csrk_matrix* h, const KernelConfig& cfg, LaunchArgs&
     a.desc = win ? h->d_xdesc : h->d_desc;
     a.colidx = win ? (const void*)h->d_colx : (cfg.kernel == 4 ? (const void*)h->d_col16 : (const void*)h->d_colidx);
     a.win = win ? h->d_win : nullptr;
+    a.wptr = win ? h->d_wptr : nullptr;
+    a.rord = win ? h->d_rord : nullptr;
+    a.n = h->m.n;
+    a.nsr = (int32_t)h->sr_ptr.size() - 1;
+    a.nnz = h->m.nnz();
 }
 
 // Resolve the launch configuration and stage plan for this handle and value type.
@@ -870,9 +887,10 @@ int autotune(csrk_matrix* h) {
         for (auto& pr : pairs)
             for (int warps : {8, 16})
                 for (int kernel : {0, 1, 2, 3, 4, 5, 6})
-                    for (int ctas : {1, 2, 3}) {
+                    for (int ctas : {1, 2, 3, 4}) {
                         if ((kernel == 1 || kernel == 3) && ctas >= 2) continue;
-                        if (ctas == 3 && (kernel < 4 || warps > 8)) continue;   // fits only small blocks
+                        if (ctas >= 3 && (kernel < 4 || warps > 8)) continue;   // fits only small blocks
+                        if (ctas == 4 && kernel != 5) continue;
                         if ((kernel == 2 || kernel == 3) && (!with_pairs || pr.first != 1 || pr.second > 16)) continue;
                         if (kernel == 4 && (!col16_available(h) || !mode3_compiled(pr.first, pr.second))) continue;
                         if (kernel == 5 && (!xwin_available(h) || !mode4_compiled(pr.first, pr.second))) continue;
@@ -1127,7 +1145,8 @@ int csrk_index_bits(csrk_handle h, int32_t* bits) {
     return CSRK_OK;
 }
 
-int csrk_xwin_info(csrk_handle h, int32_t* available, int64_t* runs, int32_t* max_window) {
+int csrk_xwin_info(csrk_handle h, int32_t* available, int64_t* runs, int32_t* max_window,
+                   int32_t* row_order) {
     if (!h) return fail(CSRK_ERR_ARG, "handle is NULL");
     if (!h->have_ptrs) return fail(CSRK_ERR_STATE, "call csrk_set_sizes or csrk_set_pointers first");
     int rc;
@@ -1136,6 +1155,7 @@ int csrk_xwin_info(csrk_handle h, int32_t* available, int64_t* runs, int32_t* ma
     if (available) *available = ok ? 1 : 0;
     if (runs) *runs = ok ? h->xwin_runs : 0;
     if (max_window) *max_window = ok ? h->max_win : 0;
+    if (row_order) *row_order = ok && h->d_rord ? 1 : 0;
     return CSRK_OK;
 }
 
@@ -1365,8 +1385,13 @@ int csrk_selftest_narrow(const double* x, int64_t n, float* by_int, float* by_cv
 const char* csrk_last_error(void) { return g_last_error.c_str(); }
 
 const char* csrk_build_info(void) {
+#ifdef CSRK_CHECKS
+    return "csrk: sm_103a; CSR-3 TMA (cp.async.bulk + mbarrier) and direct kernels; "
+           "values f64/f32/bf16; bounds checks on (status bit 1)";
+#else
     return "csrk: sm_103a; CSR-3 TMA (cp.async.bulk + mbarrier) and direct kernels; "
            "values f64/f32/bf16";
+#endif
 }
 
 }  // extern "C"

@@ -26,9 +26,9 @@ struct alignas(16) SsrDesc {
     int32_t r0, r1;   // rows [r0, r1)
     int32_t p0, p1;   // nonzeros [p0, p1)
     int32_t cbase;    // smallest column of the SSR (base of its 16-bit column coding); in
-                      // kernel 5's copy of the descriptors: first x-window run (index into
-                      // the run array)
-    int32_t aux;      // kernel 5's copy: index of the SSR's sentinel run (one past its last)
+                      // kernels 5 / 6's copy of the descriptors: the elements its x window's
+                      // runs cover
+    int32_t aux;      // kernels 5 / 6's copy: the number of runs of its x window
 };
 
 struct TileStats {
@@ -58,16 +58,25 @@ bool check_pointers(int32_t n, const std::vector<int32_t>& sr_ptr,
 // Delta-coded 16-bit columns (first entry of a row from the SSR's cbase, then steps);
 // false when some code exceeds 65,535.
 bool compress_columns(const CsrHost& b, const std::vector<SsrDesc>& desc, std::vector<uint16_t>& col16);
-// x windows of kernel 5: x is staged per SSR in runs of aligned blocks of XWIN_ALIGN
-// elements (runs at most XWIN_GAP blocks apart merged).  win holds per SSR the pairs
-// (start column, offset in the window) of its runs, then a sentinel pair (elements the
-// runs cover -- the last run may end at n --, aligned window length); xdesc is desc with
-// cbase / aux = the SSR's first run / sentinel index in pairs; colx[p] = the window
-// offset of nonzero p's column.  Returns false when some window exceeds 65,536 elements.
+// x windows of kernels 5 and 6: x is staged per SSR in runs of aligned blocks of
+// XWIN_ALIGN elements (runs at most XWIN_GAP blocks apart merged).  win holds the
+// (start column, offset in the window) pairs of all runs, SSR by SSR, SSR t's from pair
+// wptr[t] to wptr[t + 1] (plus one zero pair of padding at the end); xdesc is desc with
+// cbase = the elements SSR t's runs cover (the last run may end at n) and aux = its run
+// count; colx[p] = the window offset of nonzero p's column; max_win = the longest aligned
+// window.  Returns false when some window exceeds 65,536 elements.
+// Length order of each SSR's rows (kernels 5 and 6): ord[r0 + j] = offset from the SSR's
+// first row r0 of its j-th longest row (ties in row order).  A warp pass then takes rows of
+// similar length, so fewer of its FP64 instruction slots go to lanes that have finished.
+// Returns the FP64 issue slots (over all warp passes of 32 positions within each super-row)
+// of the natural order and of the length order.
+void build_row_order(const CsrHost& b, const std::vector<int32_t>& sr_ptr, const std::vector<SsrDesc>& desc,
+                     std::vector<uint16_t>& ord, int64_t& slots_natural, int64_t& slots_ordered);
 constexpr int32_t XWIN_ALIGN = 4;
 constexpr int32_t XWIN_GAP = 2;
 bool build_xwin(const CsrHost& b, const std::vector<SsrDesc>& desc, std::vector<SsrDesc>& xdesc,
-                std::vector<int32_t>& win, std::vector<uint16_t>& colx, int32_t& max_win);
+                std::vector<int32_t>& win, std::vector<int32_t>& wptr, std::vector<uint16_t>& colx,
+                int32_t& max_win, int64_t& total_runs);
 void build_descs(const CsrHost& b, const std::vector<int32_t>& sr_ptr,
                  const std::vector<int32_t>& ssr_ptr, std::vector<SsrDesc>& desc,
                  TileStats& st);
@@ -121,7 +130,11 @@ struct LaunchArgs {
     const int32_t* yperm; // SpMV: row r's result goes to y[yperm[r]] (fused unpermute)
     const int32_t* xflag; // pair kernels: split found an out-of-range element
     int32_t* status;
-    const int32_t* win = nullptr;   // kernel 5: x-window runs (pairs), see build_xwin
+    const int32_t* win = nullptr;   // kernels 5 / 6: x-window runs (pairs), see build_xwin
+    const int32_t* wptr = nullptr;  // kernels 5 / 6: first run of each SSR in win
+    const uint16_t* rord = nullptr; // kernels 5 / 6 (optional): rows of each SSR in length order
+    int32_t n = 0, nsr = 0;         // rows, super-rows (bounds checks of a CSRK_CHECKS build)
+    int64_t nnz = 0;                // stored entries (the same)
     TileStats stats;
     int val_type;       // ValType
     bool x_f32;
@@ -143,7 +156,7 @@ struct LaunchArgs {
 
 // Shared-memory plan of the TMA kernel for one value type.
 struct StagePlan {
-    uint32_t off_srp, off_rp, off_col, off_val, off_x, off_perm, stage_bytes, header_bytes;
+    uint32_t off_srp, off_rp, off_col, off_val, off_x, off_perm, off_ord, stage_bytes, header_bytes;
     int stages;
 };
 // x_bytes: room for the x window per stage (kernel 5, which also stages the SSR's slice of

@@ -522,7 +522,8 @@ static void xwin_ssrs(int64_t t0, int64_t t1, void* vctx) {
 }
 
 bool build_xwin(const CsrHost& b, const std::vector<SsrDesc>& desc, std::vector<SsrDesc>& xdesc,
-                std::vector<int32_t>& win, std::vector<uint16_t>& colx, int32_t& max_win) {
+                std::vector<int32_t>& win, std::vector<int32_t>& wptr, std::vector<uint16_t>& colx,
+                int32_t& max_win, int64_t& total_runs) {
     const size_t nssr = desc.size();
     std::vector<std::vector<int32_t>> runs(nssr);
     std::vector<uint8_t> ok(nssr, 1);
@@ -536,16 +537,48 @@ bool build_xwin(const CsrHost& b, const std::vector<SsrDesc>& desc, std::vector<
         }
     xdesc = desc;
     win.clear();
+    wptr.assign(nssr + 1, 0);
     max_win = 0;
+    total_runs = 0;
     for (size_t t = 0; t < nssr; ++t) {
         const std::vector<int32_t>& run = runs[t];
         const int32_t nrun = (int32_t)run.size() / 2 - 1;
-        xdesc[t].cbase = (int32_t)(win.size() / 2);
-        xdesc[t].aux = xdesc[t].cbase + nrun;
-        win.insert(win.end(), run.begin(), run.end());
+        win.insert(win.end(), run.begin(), run.end() - 2);
+        wptr[t + 1] = wptr[t] + nrun;
+        xdesc[t].cbase = run[2 * nrun];   // elements the copies cover
+        xdesc[t].aux = nrun;
         max_win = std::max(max_win, run.back());
+        total_runs += nrun;
     }
+    win.push_back(0);   // one pair of padding after the last run
+    win.push_back(0);
     return true;
+}
+
+void build_row_order(const CsrHost& b, const std::vector<int32_t>& sr_ptr, const std::vector<SsrDesc>& desc,
+                     std::vector<uint16_t>& ord, int64_t& slots_natural, int64_t& slots_ordered) {
+    const int32_t covered = sr_ptr.empty() ? 0 : sr_ptr.back();
+    ord.assign((size_t)covered, 0);
+    slots_natural = slots_ordered = 0;
+    std::vector<int32_t> rows;
+    auto len = [&](int32_t r) { return b.rowptr[r + 1] - b.rowptr[r]; };
+    for (const SsrDesc& d : desc) {
+        rows.resize((size_t)(d.r1 - d.r0));
+        for (int32_t j = 0; j < d.r1 - d.r0; ++j) rows[j] = d.r0 + j;
+        std::stable_sort(rows.begin(), rows.end(), [&](int32_t a, int32_t c) { return len(a) > len(c); });
+        for (int32_t j = 0; j < d.r1 - d.r0; ++j) ord[d.r0 + j] = (uint16_t)(rows[j] - d.r0);
+        // warp passes: 32 positions at a time inside each super-row
+        for (int32_t sr = d.s0; sr < d.s1; ++sr)
+            for (int32_t q = sr_ptr[sr]; q < sr_ptr[sr + 1]; q += 32) {
+                int32_t mn = 0, mo = 0;
+                for (int32_t k = q; k < std::min(q + 32, sr_ptr[sr + 1]); ++k) {
+                    mn = std::max(mn, len(k));
+                    mo = std::max(mo, len(rows[k - d.r0]));
+                }
+                slots_natural += mn;
+                slots_ordered += mo;
+            }
+    }
 }
 
 // ---------------------------------------------------------------- narrowing

@@ -29,6 +29,7 @@
 
 #include "csrk_internal.h"
 
+
 namespace csrk {
 namespace dev {
 
@@ -95,13 +96,10 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
         : "memory");
 }
 
-// As bulk_g2s, with the default L2 policy (for x, which later SSRs read again).
-__device__ __forceinline__ void bulk_g2s_keep(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes"
-        " [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar))
-        : "memory");
+__device__ __forceinline__ uint64_t policy_evict_normal() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
 }
 
 // ------------------------------------------------------------------ value widening
@@ -261,16 +259,20 @@ __device__ __forceinline__ void spmv_rows(int rb, int re, const int32_t* __restr
                                           const VT* __restrict__ val_s,
                                           const XT* __restrict__ x, XT* __restrict__ y,
                                           double alpha, double beta, int epi, int lane,
-                                          const int32_t* __restrict__ yperm = nullptr) {
+                                          const int32_t* __restrict__ yperm = nullptr,
+                                          const uint16_t* __restrict__ ord = nullptr, int r0 = 0) {
     constexpr int RPP = 32 / LPR;   // rows per pass
     constexpr int T = U < 4 ? U : 4;
     const int sub = lane % LPR;
     for (int base = rb; base < re; base += RPP) {
-        const int r = base + lane / LPR;
+        int r = base + lane / LPR;
         AT acc = 0;
         if constexpr (LOCAL) {
+            // LOCAL with ord: position r of the SSR's length-ordered rows is row r0 + ord[r]
+            const bool live = r < re;
+            if (ord && live) r = r0 + ord[r];
             static_assert(LPR == 1 && sizeof(CT) == 2, "window codes take one row per lane");
-            if (r < re) {
+            if (live) {
                 const int pe = rp[r + 1];
                 int c = rp[r];
                 for (; c + (U - 1) < pe; c += U) {
@@ -359,7 +361,7 @@ __device__ __forceinline__ void spmv_rows(int rb, int re, const int32_t* __restr
                 acc += __shfl_xor_sync(0xffffffffu, acc, off);
         }
         if constexpr (LOCAL) {   // the permutation slice is staged in shared memory
-            if (r < re) store_y<XT, AT>(y, yperm ? yperm[r] : r, acc, alpha, beta, epi);
+            if (base + lane < re) store_y<XT, AT>(y, yperm ? yperm[r] : r, acc, alpha, beta, epi);
         } else {
             if (r < re && sub == 0) store_y<XT, AT>(y, yperm ? __ldg(&yperm[r]) : r, acc, alpha, beta, epi);
         }
@@ -421,16 +423,19 @@ __device__ __forceinline__ void spmv_rows_ds(int rb, int re, const int32_t* __re
 // spmv_rows_ds over a staged x window (kernel 6): col_s are 16-bit window offsets, xs the
 // window in shared memory -- FP32 pairs of x in the fast path, FP64 x when the split pass
 // flagged an element (`slow`, uniform over the launch) -- and yperm, when set, the SSR's
-// staged slice of the permutation.
+// staged slice of the permutation; ord, when set, the SSR's length order of its rows (as in
+// spmv_rows).
 template <int U>
 __device__ __forceinline__ void spmv_rows_ds_win(int rb, int re, const int32_t* __restrict__ rp,
                                                  const uint16_t* __restrict__ col_s,
                                                  const ds_t* __restrict__ val_s, const void* xs, bool slow,
                                                  double* __restrict__ y, double alpha, double beta, int epi,
-                                                 int lane, const int32_t* __restrict__ yperm) {
+                                                 int lane, const int32_t* __restrict__ yperm,
+                                                 const uint16_t* __restrict__ ord, int r0) {
     for (int base = rb; base < re; base += 32) {
-        const int r = base + lane;
+        int r = base + lane;
         if (r >= re) continue;
+        if (ord) r = r0 + ord[r];   // position -> row of the length order
         const int pe = rp[r + 1];
         int c = rp[r];
         double acc;
@@ -553,11 +558,70 @@ struct TmaParams {
     const int32_t* yperm;  // SpMV: when set, row r's result goes to y[yperm[r]] (fused unpermute)
     const int32_t* xflag;  // MODE 2: non-zero when the split found an out-of-range element
     int32_t* status;
-    const int2* win;       // MODE 4: x-window runs (start, offset) per SSR, sentinel last
-    uint32_t off_srp, off_rp, off_col, off_val, off_x, off_perm, stage_bytes, header_bytes;
+    const int2* win;       // MODES 4, 5: x-window runs (start, offset), SSR by SSR
+    const int32_t* wptr;   // MODES 4, 5: first run of each SSR in win
+    const uint16_t* rord;  // MODES 4, 5 (optional): each SSR's rows in length order, as offsets
+                           // from its first row; staged at off_ord
+    // extents, read by the bounds checks of a CSRK_CHECKS build only
+    int32_t n;             // rows (and entries of x and y)
+    int32_t nsr;           // super-rows
+    int64_t nnz;           // stored entries
+    uint32_t off_srp, off_rp, off_col, off_val, off_x, off_perm, off_ord, stage_bytes, header_bytes;
     int32_t stages;
     unsigned long long timeout_ns;
 };
+
+#ifdef CSRK_CHECKS
+// Bounds checks of a CSRK_CHECKS build (a debugging build standing in for a memory
+// checker): before a warp computes a super-row, every index it is about to follow is
+// checked -- the super-row's row range inside its SSR's, each row's nonzero range inside
+// the SSR's, every column (int32: inside [0, n); CM 1, delta codes: the rebuilt column
+// inside [0, n); CM 2, window offsets: inside the staged window) and every target of the
+// fused unpermute.  A super-row with a bad index is skipped and bit 1 (value 2) of the
+// status word is set; nothing out of bounds is read or written.  The regular build
+// compiles none of this.
+template <int CM, typename CT>
+__device__ bool sr_in_bounds(int rb, int re, int r_lo, int r_hi, int64_t p_lo, int64_t p_hi,
+                             const int32_t* rp, const CT* col, int64_t cbase, int64_t limit,
+                             const int32_t* yperm, int32_t n, int lane, int32_t* status,
+                             const uint16_t* ord = nullptr) {
+    bool bad = rb < r_lo || re > r_hi || rb > re;
+    for (int pos = rb + lane; !bad && pos < re; pos += 32) {
+        const int r = ord ? r_lo + ord[pos] : pos;   // the row at position pos of a length order
+        if (r < r_lo || r >= r_hi) {
+            bad = true;
+            break;
+        }
+        const int64_t p = rp[r], q = rp[r + 1];
+        if (p < p_lo || q > p_hi || p > q) {
+            bad = true;
+            break;
+        }
+        int64_t c = 0;
+        for (int64_t k = p; k < q; ++k) {
+            if constexpr (CM == 1) c += (int64_t)col[k];
+            else c = (int64_t)col[k];
+            const int64_t abs = CM == 1 ? cbase + c : c;
+            if (abs < 0 || abs >= limit) {
+                bad = true;
+                break;
+            }
+        }
+        if (!bad && yperm && (yperm[r] < 0 || yperm[r] >= n)) bad = true;
+    }
+    if (__any_sync(0xffffffffu, bad)) {
+        if (lane == 0) report(status, 2);
+        return false;
+    }
+    return true;
+}
+
+// An SSR descriptor whose ranges leave the arrays is not staged (checks build).
+__device__ __forceinline__ bool desc_in_bounds(const SsrDesc& d, int32_t nsr, int32_t n, int64_t nnz) {
+    return 0 <= d.s0 && d.s0 <= d.s1 && d.s1 <= nsr && 0 <= d.r0 && d.r0 <= d.r1 && d.r1 <= n && 0 <= d.p0 &&
+           d.p0 <= d.p1 && d.p1 <= nnz;
+}
+#endif
 
 // Byte range [b, e) of an element slice rounded out to 16-byte boundaries.
 template <int ESZ>
@@ -604,24 +668,46 @@ __global__ void __launch_bounds__(544, 2) csr3_tma_kernel(const TmaParams P) {
     if (warp == W) {
         constexpr int CSZ = (MODE == 3 || MODE == 4 || MODE == 5) ? 2 : 4;   // bytes per stored column
         if constexpr (MODE == 4 || MODE == 5) {
-            // ---------------- producer warp: lane 0 copies the four slices, lane j the
-            // j-th x run of the window (32 runs per round)
+            // ---------------- producer warp: lane 0 copies the slices, lane j the j-th x run
+            // of the window (32 runs per round).  The metadata is loaded ahead in a short
+            // pipeline -- the next SSR's descriptor and runs, the one after's run pointers --
+            // so that no load waits on another while this SSR's stage is being refilled.
             const uint64_t pol = policy_evict_first();
+            const uint64_t polx = policy_evict_normal();   // x runs: read again by nearby SSRs
             // MODE 5 stages the FP32-pair split of x (8 bytes an element, as FP64), or the
             // FP64 x itself when the split flagged an element
             const XT* __restrict__ xg = static_cast<const XT*>(MODE == 5 && *P.xflag ? (const void*)P.x64 : P.x);
-            int i = 0;
-            bool ok = true;
-            for (int t = blockIdx.x; t < P.nssr; t += gridDim.x, ++i) {
+            const int32_t* __restrict__ WP = P.wptr;
+            const int2* __restrict__ W = P.win;
+            const int g = gridDim.x;
+            int t = blockIdx.x;
+            SsrDesc d{};
+            int2 run = make_int2(0, 0);
+            int wcur = 0, wnext = 0, wnext_e = 0;   // runs of t start at wcur; of t + g at wnext
+            if (t < P.nssr) {
+                d = P.desc[t];
+                wcur = WP[t];
+                if (lane < WP[t + 1] - wcur) run = W[wcur + lane];
+            }
+            if (t + g < P.nssr) {
+                wnext = WP[t + g];
+                wnext_e = WP[t + g + 1];
+            }
+            for (int i = 0; t < P.nssr; t += g, ++i) {
                 const int s = i % S;
-                const SsrDesc d = P.desc[t];
-                const int2 sent = P.win[d.aux];   // (elements covered, aligned length)
-                const int k = d.cbase + lane;
-                int2 run = make_int2(0, 0), nxt = make_int2(0, 0);
-                if (k < d.aux) {
-                    run = P.win[k];
-                    nxt = P.win[k + 1];
+                const int tn = t + g, tnn = t + 2 * g;
+                SsrDesc dn{};
+                int2 run_n = make_int2(0, 0);
+                int w2 = 0, w2e = 0;
+                if (tn < P.nssr) {
+                    dn = P.desc[tn];
+                    if (lane < wnext_e - wnext) run_n = W[wnext + lane];
                 }
+                if (tnn < P.nssr) {
+                    w2 = WP[tnn];
+                    w2e = WP[tnn + 1];
+                }
+                bool ok = true;
                 if (lane == 0 && i >= S && !mbar_wait_bounded(&empty[s], ((i / S) - 1) & 1, P.timeout_ns)) {
                     report(P.status, 1);
                     ok = false;
@@ -629,15 +715,43 @@ __global__ void __launch_bounds__(544, 2) csr3_tma_kernel(const TmaParams P) {
                 if (!__shfl_sync(0xffffffffu, ok, 0)) break;
                 unsigned char* st = stage0 + (size_t)s * P.stage_bytes;
                 XT* xs = reinterpret_cast<XT*>(st + P.off_x);
-                const uint32_t xexact = (uint32_t)sent.x * (uint32_t)sizeof(XT);
+#ifdef CSRK_CHECKS
+                {   // a descriptor or a run outside its array: stage nothing, consumers skip the SSR
+                    const int k = lane;
+                    bool bad = !desc_in_bounds(d, P.nsr, P.n, P.nnz) || d.aux < 0 ||
+                               (int64_t)d.cbase * (int64_t)sizeof(XT) > (int64_t)(P.off_perm - P.off_x);
+                    if (!bad && k < d.aux) {
+                        const int end = k + 1 == d.aux ? d.cbase : W[wcur + k + 1].y;
+                        bad = run.x < 0 || run.y < 0 || end < run.y || (int64_t)run.x + (end - run.y) > P.n;
+                    }
+                    if (__any_sync(0xffffffffu, bad)) {
+                        if (lane == 0) {
+                            report(P.status, 2);
+                            SsrDesc e = d;
+                            e.s1 = e.s0;   // no super-rows
+                            dsc[s] = e;
+                            mbar_arrive_expect_tx(&full[s], 0);
+                        }
+                        __syncwarp();
+                        d = dn;
+                        run = run_n;
+                        wcur = wnext;
+                        wnext = w2;
+                        wnext_e = w2e;
+                        continue;
+                    }
+                }
+#endif
+                const int nrun = d.aux;                 // runs of this SSR's window
+                const uint32_t xexact = (uint32_t)d.cbase * (uint32_t)sizeof(XT);   // elements covered
                 const uint32_t xbulk = xexact & ~15u;
                 if (lane == 0) {
                     dsc[s] = d;
                     // the window's last run may end at n off a 16-byte boundary: its last
                     // (at most 3) elements are copied with plain loads, before the arrive
                     if (xbulk != xexact) {
-                        const int2 lr = P.win[d.aux - 1];
-                        const int len = sent.x - lr.y;
+                        const int2 lr = W[wcur + nrun - 1];
+                        const int len = d.cbase - lr.y;
                         for (int e = len - (int)((xexact - xbulk) / sizeof(XT)); e < len; ++e)
                             xs[lr.y + e] = xg[lr.x + e];
                     }
@@ -648,8 +762,12 @@ __global__ void __launch_bounds__(544, 2) csr3_tma_kernel(const TmaParams P) {
                     slice16<CSZ>(d.p0, d.p1, o_col, b_col);
                     slice16<sizeof(VT)>(d.p0, d.p1, o_val, b_val);
                     if (P.yperm) slice16<4>(d.r0, d.r1, o_pm, b_pm);   // the fused unpermute's targets
-                    mbar_arrive_expect_tx(&full[s], b_srp + b_rp + b_col + b_val + xbulk + b_pm);
+                    uint32_t b_ord = 0;
+                    int64_t o_ord = 0;
+                    if (P.rord) slice16<2>(d.r0, d.r1, o_ord, b_ord);  // the rows' length order
+                    mbar_arrive_expect_tx(&full[s], b_srp + b_rp + b_col + b_val + xbulk + b_pm + b_ord);
                     if (b_pm) bulk_g2s(st + P.off_perm, P.yperm + o_pm, b_pm, &full[s], pol);
+                    if (b_ord) bulk_g2s(st + P.off_ord, P.rord + o_ord, b_ord, &full[s], pol);
                     bulk_g2s(st + P.off_srp, P.sr_ptr + o_srp, b_srp, &full[s], pol);
                     bulk_g2s(st + P.off_rp, P.rowptr + o_rp, b_rp, &full[s], pol);
                     if (b_col)
@@ -659,19 +777,23 @@ __global__ void __launch_bounds__(544, 2) csr3_tma_kernel(const TmaParams P) {
                         bulk_g2s(st + P.off_val, static_cast<const VT*>(P.vals) + o_val, b_val, &full[s], pol);
                 }
                 __syncwarp();
-                // the runs, 32 per round (after the arrive, so the expected bytes come first)
-                for (int k0 = 0; d.cbase + k0 < d.aux; k0 += 32) {
-                    const int kk = k + k0;
-                    if (kk < d.aux) {
-                        if (k0 > 0) {
-                            run = P.win[kk];
-                            nxt = P.win[kk + 1];
-                        }
-                        const int end = (kk + 1 == d.aux) ? nxt.x : nxt.y;
-                        const uint32_t b = ((uint32_t)(end - run.y) * (uint32_t)sizeof(XT)) & ~15u;
-                        if (b) bulk_g2s_keep(xs + run.y, xg + run.x, b, &full[s]);
+                // the runs, 32 per round (after the arrive, so the expected bytes come first);
+                // a run ends where the next begins in the window, the last at the SSR's count
+                for (int k0 = 0; k0 < nrun; k0 += 32) {
+                    const int k = k0 + lane;
+                    const int2 r = k0 == 0 ? run : (k < nrun ? W[wcur + k] : make_int2(0, 0));
+                    const int next_base = __shfl_down_sync(0xffffffffu, r.y, 1);
+                    if (k < nrun) {
+                        const int end = k + 1 == nrun ? d.cbase : (lane == 31 ? W[wcur + k + 1].y : next_base);
+                        const uint32_t b = ((uint32_t)(end - r.y) * (uint32_t)sizeof(XT)) & ~15u;
+                        if (b) bulk_g2s(xs + r.y, xg + r.x, b, &full[s], polx);
                     }
                 }
+                d = dn;
+                run = run_n;
+                wcur = wnext;
+                wnext = w2;
+                wnext_e = w2e;
             }
         } else if (lane == 0) {
             // ---------------- producer: one elected lane issues the bulk copies
@@ -684,6 +806,16 @@ __global__ void __launch_bounds__(544, 2) csr3_tma_kernel(const TmaParams P) {
                     break;
                 }
                 const SsrDesc d = P.desc[t];
+#ifdef CSRK_CHECKS
+                if (!desc_in_bounds(d, P.nsr, P.n, P.nnz)) {   // stage nothing, consumers skip it
+                    report(P.status, 2);
+                    SsrDesc e = d;
+                    e.s1 = e.s0;
+                    dsc[s] = e;
+                    mbar_arrive_expect_tx(&full[s], 0);
+                    continue;
+                }
+#endif
                 dsc[s] = d;
                 unsigned char* st = stage0 + (size_t)s * P.stage_bytes;
                 uint32_t b_srp, b_rp, b_col, b_val;
@@ -736,6 +868,25 @@ __global__ void __launch_bounds__(544, 2) csr3_tma_kernel(const TmaParams P) {
         for (int j = first; j < nsr; j += W) {
             const int sr = d.s0 + j;
             const int rb = srp[sr], re = srp[sr + 1];
+#ifdef CSRK_CHECKS
+            {
+                const int32_t* yp = (MODE == 4 || MODE == 5) && P.yperm
+                                        ? reinterpret_cast<const int32_t*>(st + P.off_perm) - (d.r0 & ~3)
+                                        : P.yperm;
+                bool ok;
+                if constexpr (MODE == 3)
+                    ok = sr_in_bounds<1>(rb, re, d.r0, d.r1, d.p0, d.p1, rp, col16, d.cbase, P.n, yp, P.n, lane,
+                                         P.status);
+                else if constexpr (MODE == 4 || MODE == 5)
+                    ok = sr_in_bounds<2>(rb, re, d.r0, d.r1, d.p0, d.p1, rp, col16, 0, d.cbase, yp, P.n, lane,
+                                         P.status,
+                                         P.rord ? reinterpret_cast<const uint16_t*>(st + P.off_ord) - (d.r0 & ~7)
+                                                : nullptr);
+                else
+                    ok = sr_in_bounds<0>(rb, re, d.r0, d.r1, d.p0, d.p1, rp, col, 0, P.n, yp, P.n, lane, P.status);
+                if (!ok) continue;
+            }
+#endif
             if constexpr (MODE == 2)
                 spmv_rows_ds<U>(rb, re, rp, col, val, reinterpret_cast<const xpair*>(P.x), P.x64,
                                 slow, y, P.alpha, P.beta, P.epi, lane, P.yperm);
@@ -748,12 +899,16 @@ __global__ void __launch_bounds__(544, 2) csr3_tma_kernel(const TmaParams P) {
             else if constexpr (MODE == 5)
                 spmv_rows_ds_win<U>(rb, re, rp, col16, val, st + P.off_x, slow, y, P.alpha, P.beta, P.epi, lane,
                                     P.yperm ? reinterpret_cast<const int32_t*>(st + P.off_perm) - (d.r0 & ~3)
-                                            : nullptr);
+                                            : nullptr,
+                                    P.rord ? reinterpret_cast<const uint16_t*>(st + P.off_ord) - (d.r0 & ~7)
+                                           : nullptr,
+                                    d.r0);
             else if constexpr (MODE == 4)
                 spmv_rows<VT, XT, AT, 1, U, uint16_t, true>(
                     rb, re, rp, col16, val, reinterpret_cast<const XT*>(st + P.off_x), y, P.alpha, P.beta,
                     P.epi, lane,
-                    P.yperm ? reinterpret_cast<const int32_t*>(st + P.off_perm) - (d.r0 & ~3) : nullptr);
+                    P.yperm ? reinterpret_cast<const int32_t*>(st + P.off_perm) - (d.r0 & ~3) : nullptr,
+                    P.rord ? reinterpret_cast<const uint16_t*>(st + P.off_ord) - (d.r0 & ~7) : nullptr, d.r0);
             else
                 spmm_rows<VT, XT, AT, LPR, U>(rb, re, rp, col, val, x, P.ldx, y, P.ldy, P.k,
                                                P.alpha, P.beta, P.epi, lane);
@@ -780,9 +935,20 @@ __global__ void __launch_bounds__(512, 1) csr3_direct_kernel(const TmaParams P) 
     const VT* __restrict__ vals = static_cast<const VT*>(P.vals);
     for (int t = blockIdx.x; t < P.nssr; t += gridDim.x) {
         const SsrDesc d = P.desc[t];
+#ifdef CSRK_CHECKS
+        if (!desc_in_bounds(d, P.nsr, P.n, P.nnz)) {
+            if (threadIdx.x == 0) report(P.status, 2);
+            continue;
+        }
+#endif
         for (int sr = d.s0 + warp; sr < d.s1; sr += W) {
             const int rb = __ldg(&P.sr_ptr[sr]), re = __ldg(&P.sr_ptr[sr + 1]);
             const int32_t* cols = static_cast<const int32_t*>(P.colidx);
+#ifdef CSRK_CHECKS
+            if (!sr_in_bounds<0>(rb, re, d.r0, d.r1, d.p0, d.p1, P.rowptr, cols, 0, P.n, P.yperm, P.n, lane,
+                                 P.status))
+                continue;
+#endif
             if constexpr (MODE == 2)
                 spmv_rows_ds<U>(rb, re, P.rowptr, cols, vals, reinterpret_cast<const xpair*>(P.x),
                                 P.x64, slow, y, P.alpha, P.beta, P.epi, lane, P.yperm);

@@ -13,6 +13,8 @@ namespace dev {
 
 // Blocks of `kern` that fit on one SM at once with this block size and dynamic shared
 // memory (at least 1), remembered per (device, threads, shared memory) for each kernel.
+// When the query fails (e.g. while a stream is being captured into a graph) nothing is
+// remembered and no limit is applied.
 template <typename K>
 static int resident_blocks(K kern, int dev, int threads, int smem) {
     struct Entry {
@@ -27,7 +29,7 @@ static int resident_blocks(K kern, int dev, int threads, int smem) {
     int blocks = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, threads, smem) != cudaSuccess) {
         cudaGetLastError();
-        blocks = 1;
+        return 1 << 20;
     }
     blocks = std::max(blocks, 1);
     if (used < 16) cache[used++] = Entry{dev, threads, smem, blocks};
@@ -58,8 +60,14 @@ static int launch_one(const LaunchArgs& a, const KernelConfig& cfg, const StageP
     P.xflag = a.xflag;
     P.status = a.status;
     P.win = reinterpret_cast<const int2*>(a.win);
+    P.wptr = a.wptr;
+    P.n = a.n;
+    P.nsr = a.nsr;
+    P.nnz = a.nnz;
     P.off_x = plan.off_x;
     P.off_perm = plan.off_perm;
+    P.off_ord = plan.off_ord;
+    P.rord = a.rord;
     P.off_srp = plan.off_srp;
     P.off_rp = plan.off_rp;
     P.off_col = plan.off_col;

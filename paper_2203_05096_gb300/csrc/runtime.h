@@ -49,11 +49,14 @@ struct csrk_matrix {
     int col16_ok = -1;             // offsets usable with the current pointers; -1 unknown
     // kernel 5: per-SSR x windows (build_xwin), built and uploaded on first use
     SsrDesc* d_xdesc = nullptr;    // descriptors with the SSR's window runs in cbase / aux
-    int32_t* d_win = nullptr;      // (start, offset) run pairs, a sentinel pair per SSR
+    int32_t* d_win = nullptr;      // (start, offset) run pairs, SSR by SSR
+    int32_t* d_wptr = nullptr;     // first run of each SSR in d_win (nssr + 1)
     uint16_t* d_colx = nullptr;    // window offset of each nonzero's column
     int xwin_ok = -1;              // windows usable with the current pointers; -1 unknown
     int32_t max_win = 0;           // longest window (elements, multiple of 4)
-    int64_t xwin_runs = 0;         // runs over all SSRs (sentinels not counted)
+    int64_t xwin_runs = 0;         // runs over all SSRs
+    uint16_t* d_rord = nullptr;    // rows of each SSR in length order (kernels 5 / 6), uploaded
+                                   // only when it saves FP64 issue slots (irregular rows)
     void* d_vals[4] = {nullptr, nullptr, nullptr, nullptr};   // by ValType
     int pairs_ok = -1;             // FP32-pair path usable (values in range); -1 unknown
     int32_t* d_sr_ptr = nullptr;

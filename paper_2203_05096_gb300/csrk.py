@@ -71,19 +71,21 @@ _PROTOS = {
     "csrk_batch_device_status": [_vp, _pi32],
     "csrk_batch_destroy": [_vp],
     "csrk_spmv_static_scratch": [_i32, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _d, _vp, _d, _vp, _vp],
-    "csrk_xwin_info": [_vp, _vp, _vp, _vp],
+    "csrk_xwin_info": [_vp, _vp, _vp, _vp, _vp],
 }
 
 
 def lib(build_if_missing: bool = True):
-    """Load libcsrk.so (building it first when the sources are newer)."""
+    """Load libcsrk.so (building it first when the sources are newer); with the environment
+    variable CSRK_CHECKS=1, the bounds-checked build libcsrk_checks.so instead."""
     global _LIB
     if _LIB is None:
-        path = _build.LIB
+        checks = os.environ.get("CSRK_CHECKS") == "1"
+        path = _build.LIB_CHECKS if checks else _build.LIB
         if build_if_missing:
-            path = _build.build()
+            path = _build.build(checks=checks)
         if not os.path.exists(path):
-            raise RuntimeError(f"libcsrk.so not found at {path}; run __graft_entry__.build()")
+            raise RuntimeError(f"{os.path.basename(path)} not found at {path}; run __graft_entry__.build()")
         h = ctypes.CDLL(path)
         for name, args in _PROTOS.items():
             fn = getattr(h, name)
@@ -249,11 +251,12 @@ def tuned_config(h):
 
 
 def xwin_info(h):
-    """Kernel 5's x windows: dict(available, runs, max_window)."""
-    av, mw = ctypes.c_int32(), ctypes.c_int32()
+    """The x windows of kernels 5 and 6: dict(available, runs, max_window, row_order)."""
+    av, mw, ro = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
     runs = ctypes.c_int64()
-    _check(lib().csrk_xwin_info(h, ctypes.byref(av), ctypes.byref(runs), ctypes.byref(mw)), "csrk_xwin_info")
-    return dict(available=bool(av.value), runs=runs.value, max_window=mw.value)
+    _check(lib().csrk_xwin_info(h, ctypes.byref(av), ctypes.byref(runs), ctypes.byref(mw), ctypes.byref(ro)),
+           "csrk_xwin_info")
+    return dict(available=bool(av.value), runs=runs.value, max_window=mw.value, row_order=bool(ro.value))
 
 
 def set_config(h, kernel=-1, lanes=-1, unroll=-1, warps=-1, stages=-1, ctas=-1):

@@ -33,3 +33,15 @@ def test_whole_job_rate_and_replicas():
     # N replicas each doing W units in the slowest rank's time t: N * W / t
     assert bench.whole_job_rate(4, 1.0e9, 2.0) == 4 * 1.0e9 / 2.0e-3
     assert bench.max_over_ranks(3.5, None, "cpu") == 3.5
+
+
+def test_algorithmic_bytes_window_kernel_by_hand():
+    # kernels 5 / 6: 2-byte window codes, plus the run table (8 bytes a run, 4 bytes of run
+    # pointer per SSR and one more) and, when the rows' length order is staged, 2 bytes a row
+    n, nnz = 128 ** 3, 55_742_968
+    nsr, nssr = n // 32, n // 64
+    base = bench.alg_bytes_spmv(n, nnz, nsr, nssr, col_bytes=2)
+    assert bench.col_bytes_of({"kernel": 5}) == bench.col_bytes_of({"kernel": 6}) == 2
+    assert bench.alg_bytes_spmv(n, nnz, nsr, nssr, col_bytes=2, runs=300_000) == base + 8 * 300_000 + 4 * (nssr + 1)
+    assert bench.alg_bytes_spmv(n, nnz, nsr, nssr, col_bytes=2, runs=300_000, row_order=True) == \
+        base + 8 * 300_000 + 4 * (nssr + 1) + 2 * n

@@ -252,3 +252,32 @@ def test_xwin_pairs_in_cg():
     true = np.linalg.norm(b - ospmv.csr_spmv(a.n, a.rowptr, a.colidx, a.vals, xt.cpu().numpy())) / np.linalg.norm(b)
     assert true <= 1.05e-10
     csrk.destroy(h)
+
+
+# ------------------------------------------------------------------ length order of irregular rows
+@pytest.mark.parametrize("kernel", [5, 6])
+def test_xwin_row_length_order(kernel):
+    """Rows of unequal length (FEM-like, 13-24 entries; a random pattern with empty rows):
+    the window kernels hand each SSR's rows to warp passes in order of length.  Each row's
+    arithmetic is unchanged, so kernel 5 stays bit-identical to kernel 0; kernel 6 within
+    the FP64 bound."""
+    for a in (synth.fem_like(14, 7), synth.random_pattern(4000, 0.004, 87, empty_rows=100)):
+        h = make(a, 32, 4)
+        info = csrk.xwin_info(h)
+        assert info["available"] and info["row_order"]
+        x = synth.uniform_vector(a.n, 88)
+        y0 = synth.uniform_vector(a.n, 89)
+        csrk.set_config(h, kernel=0, lanes=1, unroll=8, warps=8)
+        ref = gpu_spmv(h, x, 0.75, -1.5, y0)
+        csrk.set_config(h, kernel=kernel, lanes=1, unroll=8, warps=8)
+        got = gpu_spmv(h, x, 0.75, -1.5, y0)
+        if kernel == 5:
+            assert np.array_equal(got, ref)
+        assert_close(got, a, a.vals, x, 0.75, -1.5, y0)
+        perm = csrk.export(h)["perm"]
+        got_p = gpu_spmv(h, x[perm], flags=csrk.VEC_PERMUTED)
+        y = np.empty_like(got_p)
+        y[perm] = got_p
+        assert_close(y, a, a.vals, x)
+        csrk.destroy(h)
+
