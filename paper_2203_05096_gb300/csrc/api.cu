@@ -432,10 +432,15 @@ int resolve_config(csrk_matrix* h, int vt, KernelConfig& cfg, StagePlan& plan, i
         else if (cfg.kernel >= 4) cfg.kernel = 0;   // 4, 5, 6
     }
     const bool forced = h->kernel_forced && vt == (int)h->dtype && !spmm;
-    // other value types (a mixed solve's inner product) take the 16-bit column coding
-    // whenever it fits: their bytes are mostly indices
-    if (vt != (int)h->dtype && cfg.kernel == 0 && mode3_compiled(cfg.lanes, cfg.unroll) && col16_available(h))
+    // other value types (a mixed solve's inner product) take the shape timed for them on
+    // these pointers (tune_inner), else the 16-bit column coding whenever it fits: their
+    // bytes are mostly indices
+    if (vt != (int)h->dtype && !spmm && vt < 4 && h->inner_gen[vt] == h->generation) {
+        cfg = h->inner_cfg[vt];
+    } else if (vt != (int)h->dtype && cfg.kernel == 0 && mode3_compiled(cfg.lanes, cfg.unroll) &&
+               col16_available(h)) {
         cfg.kernel = 4;
+    }
     if ((cfg.kernel == 2 || cfg.kernel == 3 || cfg.kernel == 6) && (vt != VAL_F64 || !pairs_available(h))) {
         if (forced)
             return fail(CSRK_ERR_UNSUPPORTED, "the FP32-pair FP64 path needs FP64 values in [2^-39, 2^60] "
@@ -678,6 +683,60 @@ int launch_spmv_dev(csrk_matrix* h, int vt, const void* x, void* y, double alpha
     int e = launch_csr3(a, cfg, plan, s);
     if (e == -1) return fail(CSRK_ERR_UNSUPPORTED, "kernel variant not compiled for this configuration");
     if (e) return cuda_fail((cudaError_t)e, "CSR-3 kernel launch");
+    return CSRK_OK;
+}
+
+int tune_inner(csrk_matrix* h, int vt, const void* x, void* y) {
+    if (vt == (int)h->dtype || vt >= 4) return CSRK_OK;
+    NvtxRange range("csrk tune inner");
+    cudaStream_t s;
+    CK_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking), "tune stream");
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    KernelConfig best;
+    float best_us = 1e30f;
+    const bool win = xwin_available(h), c16 = col16_available(h);
+    for (int kernel : {4, 5})
+        for (int unroll : {4, 8})
+            for (int warps : {4, 8, 16})
+                for (int ctas : {2, 3, 4}) {
+                    if ((kernel == 4 && !c16) || (kernel == 5 && !win)) continue;
+                    if ((warps == 16 && ctas > 2) || (ctas == 4 && kernel != 5)) continue;
+                    KernelConfig c;
+                    c.kernel = kernel;
+                    c.lanes = 1;
+                    c.unroll = unroll;
+                    c.warps = warps;
+                    c.ctas = ctas;
+                    c.stages = 0;
+                    h->inner_cfg[vt] = c;
+                    h->inner_gen[vt] = h->generation;
+                    KernelConfig r;
+                    StagePlan plan;
+                    if (resolve_config(h, vt, r, plan, 4, x) || r.kernel != kernel) continue;   // does not fit
+                    bool ok = launch_spmv_dev(h, vt, x, y, 1.0, 0.0, true, true, nullptr, s) == CSRK_OK;
+                    cudaEventRecord(e0, s);
+                    for (int i = 0; ok && i < 5; ++i) ok = launch_spmv_dev(h, vt, x, y, 1.0, 0.0, true, true, nullptr, s) == CSRK_OK;
+                    cudaEventRecord(e1, s);
+                    if (!ok || cudaEventSynchronize(e1) != cudaSuccess) continue;
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    if (ms * 200.f < best_us) {
+                        best_us = ms * 200.f;
+                        best = c;
+                    }
+                }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamDestroy(s);
+    cudaGetLastError();
+    if (best_us >= 1e29f) {   // nothing timed: leave the default shape to resolve_config
+        h->inner_gen[vt] = ~0ull;
+        return CSRK_OK;
+    }
+    h->inner_cfg[vt] = best;
+    h->inner_gen[vt] = h->generation;
     return CSRK_OK;
 }
 

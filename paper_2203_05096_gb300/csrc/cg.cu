@@ -528,6 +528,8 @@ int cg_solve(csrk_matrix* h, const double* b, double* x, double rtol, int32_t ma
         // one eager cycle on the capture stream first, so every kernel's attributes are set
         // and nothing but launches is recorded; its effect is undone by re-initialising
         CK_CUDA(cudaStreamSynchronize(s), "synchronise");
+        // the inner product's launch shape, timed on these pointers at the first mixed solve
+        if (mixed && h->inner_gen[vt] != h->generation && (rc = tune_inner(h, vt, w->p32, w->q32))) return rc;
         if ((rc = enqueue_cycle(h, vt, 1, w->cap))) return rc;
         CK_CUDA(cudaStreamSynchronize(w->cap), "synchronise");
         cg_init<<<g, RED_THREADS, 0, w->cap>>>(n, w->b, w->x, w->r, w->p, mixed ? w->p32 : nullptr, rtol,

@@ -799,13 +799,16 @@ __global__ void __launch_bounds__(544, 2) csr3_tma_kernel(const TmaParams P) {
             // ---------------- producer: one elected lane issues the bulk copies
             const uint64_t pol = policy_evict_first();
             int i = 0;
+            SsrDesc dn{};   // the next SSR's descriptor, loaded ahead of the wait for its stage
+            if ((int)blockIdx.x < P.nssr) dn = P.desc[blockIdx.x];
             for (int t = blockIdx.x; t < P.nssr; t += gridDim.x, ++i) {
                 const int s = i % S;
+                const SsrDesc d = dn;
+                if (t + (int)gridDim.x < P.nssr) dn = P.desc[t + gridDim.x];
                 if (i >= S && !mbar_wait_bounded(&empty[s], ((i / S) - 1) & 1, P.timeout_ns)) {
                     report(P.status, 1);
                     break;
                 }
-                const SsrDesc d = P.desc[t];
 #ifdef CSRK_CHECKS
                 if (!desc_in_bounds(d, P.nsr, P.n, P.nnz)) {   // stage nothing, consumers skip it
                     report(P.status, 2);

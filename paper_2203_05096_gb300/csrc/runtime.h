@@ -73,6 +73,11 @@ struct csrk_matrix {
     struct CgWork* cg = nullptr;
     // bumped whenever pointers or the launch shape change (invalidates captured graphs)
     unsigned long long generation = 0;
+    // launch shape of the inner SpMV of a mixed-precision solve, by value type (FP32 /
+    // BF16 values, FP32 x and accumulation), timed on the current pointers at the first
+    // solve of that precision (tune_inner); valid while generation is unchanged
+    KernelConfig inner_cfg[4];
+    unsigned long long inner_gen[4] = {~0ull, ~0ull, ~0ull, ~0ull};
 };
 
 namespace csrk {
@@ -115,6 +120,10 @@ int compute(csrk_matrix* h, int32_t k, bool spmm, double alpha, const void* X, i
 void free_cg(csrk_matrix* h);
 int launch_spmv_dev(csrk_matrix* h, int vt, const void* x, void* y, double alpha, double beta,
                     bool x_f32, bool acc_f32, const int32_t* skip, cudaStream_t s);
+// Time launch shapes of the vt-valued SpMV with FP32 x and accumulation (the inner product
+// of a mixed-precision solve) on the current pointers and keep the fastest for vt.  x, y:
+// device FP32 vectors of n (contents irrelevant).  Runs on a private stream, synchronously.
+int tune_inner(csrk_matrix* h, int vt, const void* x, void* y);
 
 }  // namespace rt
 }  // namespace csrk
