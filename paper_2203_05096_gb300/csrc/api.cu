@@ -697,12 +697,14 @@ int tune_inner(csrk_matrix* h, int vt, const void* x, void* y) {
     KernelConfig best;
     float best_us = 1e30f;
     const bool win = xwin_available(h), c16 = col16_available(h);
+    // small blocks in numbers as well: the narrow product's consumers are fast, so many
+    // independent stage rings per SM keep more copies in flight
     for (int kernel : {4, 5})
         for (int unroll : {4, 8})
-            for (int warps : {4, 8, 16})
-                for (int ctas : {2, 3, 4}) {
+            for (int warps : {2, 4, 8, 16})
+                for (int ctas : {2, 3, 4, 6, 8}) {
                     if ((kernel == 4 && !c16) || (kernel == 5 && !win)) continue;
-                    if ((warps == 16 && ctas > 2) || (ctas == 4 && kernel != 5)) continue;
+                    if ((warps == 16 && ctas > 2) || (warps == 8 && ctas > 4) || (warps <= 4 && ctas < 4)) continue;
                     KernelConfig c;
                     c.kernel = kernel;
                     c.lanes = 1;
