@@ -60,14 +60,12 @@ WORKLOAD = ("128^3 7-point and 27-point random diagonally dominant stencils (FP6
 SR, SSR = 32, 8
 MATRICES = (("stencil7", 7), ("stencil27", 27))
 
-# DRAM traffic per launch of the dominant kernel from an ncu capture, keyed by (matrix,
-# dtype, kernel number) and valid only for the kernel source it was taken on.  Each entry
-# is a 96^3 capture (profiles/csr3_tma_27pt_96cubed_f64.md: 299.20 MB, kernel 0;
-# profiles/csr3_tma_k4_27pt_96cubed_f64.md: 252.25 MB, kernel 4) scaled to 128^3 by
-# nonzeros.
+# DRAM traffic per launch of the dominant kernel from an ncu capture of the 128^3 launch,
+# keyed by (matrix, dtype, kernel number) and valid only for the kernel source it was
+# taken on (the profiles directory holds each capture's command and figures).
 NCU_TRAFFIC = {
-    ("stencil27", "f64", 0): {"bytes": 712_940_980, "kernel_hash": "871b5d682a86"},
-    ("stencil27", "f64", 4): {"bytes": 601_073_144, "kernel_hash": "150e04d362cd"},
+    ("stencil27", "f64", 4): {"bytes": 599_657_728, "kernel_hash": "150e04d362cd"},
+    ("stencil27", "f64", 5): {"bytes": 604_789_248, "kernel_hash": "7e5e22f33fe6"},
 }
 
 

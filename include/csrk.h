@@ -186,7 +186,11 @@ int csrk_index_bits(csrk_handle h, int32_t* bits);
 int csrk_set_pointers(csrk_handle h, int32_t nsr, const int32_t* sr_ptr, int32_t nssr,
                       const int32_t* ssr_ptr);
 
-/* csrk_spmv: y = alpha*A*x + beta*y with A's stored dtype.
+/* csrk_spmv: y = alpha*A*x + beta*y with A's stored dtype -- the paper's problem
+ * statement y = A x over the CSR-k arrays (Sec. 1; the CSR-3 loop nest of Listing 1, whose
+ * GPU forms are Listings 3 and 4, Sec. 3), with the BLAS scaling by alpha and beta added.
+ * Each row's result is its stored entries' products summed in stored order (FP64 kernels);
+ * the row grouping into super-rows and super-super-rows only decides who computes it.
  *   x, y    n entries, FP64 (FP32 with CSRK_X_F32), in the input numbering unless
  *           CSRK_VEC_PERMUTED; device pointers unless CSRK_HOST_VECTORS
  *   beta    0 means y is write-only (its old contents, even NaN, are not read)
@@ -200,7 +204,10 @@ int csrk_set_pointers(csrk_handle h, int32_t nsr, const int32_t* sr_ptr, int32_t
 int csrk_spmv(csrk_handle h, double alpha, const void* x, double beta, void* y,
               unsigned flags, void* stream);
 
-/* csrk_spmm: Y = alpha*A*X + beta*Y for k right-hand sides, 1 <= k <= 64.
+/* csrk_spmm: Y = alpha*A*X + beta*Y for k right-hand sides, 1 <= k <= 64: the product of
+ * Sec. 1 applied to k vectors at once over the same CSR-k arrays (Listing 1's loop nest,
+ * a row's k sums formed together so A is read once); not in the paper, which multiplies
+ * one vector.
  *   X       n x k, row-major, leading dimension ldx >= k (entry (i,c) at X[i*ldx + c])
  *   Y       n x k, row-major, leading dimension ldy >= k
  * Same flags, dtypes, numbering and errors as csrk_spmv; column c of Y is exactly what
@@ -434,7 +441,8 @@ int csrk_xwin_info(csrk_handle h, int32_t* available, int64_t* runs, int32_t* ma
  *            pairs: (1,4) (1,8) (1,16) (1,32) (2,8) (2,16) (4,8) (8,8) (32,4)
  *   warps    consumer warps per thread block (1..16)
  *   stages   shared-memory pipeline depth of the TMA kernel (0 = as many as fit)
- *   ctas     thread blocks per SM (TMA kernel); 0 = auto: 2 when two stages fit, else 1
+ *   ctas     thread blocks per SM (TMA kernel), 1-8 (never more than fit at once); 0 = auto:
+ *            2 when two stages fit, else 1
  * Once the pointer arrays exist and a device has been used, the values reported are the
  * ones the next launch resolves to (stages and ctas filled in, a TMA kernel that does not
  * fit replaced by the direct kernel). */

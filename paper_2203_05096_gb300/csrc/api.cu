@@ -1406,7 +1406,7 @@ int csrk_set_config(csrk_handle h, int32_t kernel, int32_t lanes, int32_t unroll
         c.stages = stages;
     }
     if (ctas >= 0) {
-        if (ctas > 4) return fail(CSRK_ERR_ARG, "ctas must be 0 (auto) or in [1, 4]");
+        if (ctas > 8) return fail(CSRK_ERR_ARG, "ctas must be 0 (auto) or in [1, 8]");
         c.ctas = ctas;
     }
     h->cfg = c;
