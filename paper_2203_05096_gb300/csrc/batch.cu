@@ -508,7 +508,8 @@ __global__ void __launch_bounds__(VT_THREADS) bcg_dot(const Chunk* __restrict__ 
     chunk_partial(v, k, partials + (int64_t)blockIdx.x * 32);
 }
 
-// X += alpha P; R -= alpha Q; partial r.r
+// R -= alpha Q; partial r.r (X += alpha P is done by bcg_update_p, which reads P anyway,
+// when X is NULL here)
 template <typename TQ>
 __global__ void __launch_bounds__(VT_THREADS) bcg_update_xr(const Chunk* __restrict__ chunks, const BatchMat* mats,
                                                             const int32_t* sys_off, const SysState* st,
@@ -526,9 +527,11 @@ __global__ void __launch_bounds__(VT_THREADS) bcg_update_xr(const Chunk* __restr
         for (int u = 0; u < CHUNK_ILP; ++u) {
             const int64_t i = e + u * VT_THREADS;
             if (i < e1) {
-                x[u] = X[i];
+                if (X) {
+                    x[u] = X[i];
+                    p[u] = P[i];
+                }
                 r[u] = R[i];
-                p[u] = P[i];
                 q[u] = as_f64(Q[i]);
             }
         }
@@ -536,7 +539,7 @@ __global__ void __launch_bounds__(VT_THREADS) bcg_update_xr(const Chunk* __restr
         for (int u = 0; u < CHUNK_ILP; ++u) {
             const int64_t i = e + u * VT_THREADS;
             if (i < e1) {
-                X[i] = x[u] + alpha * p[u];
+                if (X) X[i] = x[u] + alpha * p[u];
                 const double rn = r[u] - alpha * q[u];
                 R[i] = rn;
                 v += rn * rn;
@@ -546,29 +549,34 @@ __global__ void __launch_bounds__(VT_THREADS) bcg_update_xr(const Chunk* __restr
     chunk_partial(v, k, partials + (int64_t)blockIdx.x * 32);
 }
 
-// P = R + beta P (and P32 = P rounded to FP32 when given)
+// P = R + beta P (and P32 = P rounded to FP32 when given); with X given, first X += alpha P
+// with the old P (the iteration's x update, moved here from bcg_update_xr so that P is read
+// once per iteration instead of twice)
 __global__ void __launch_bounds__(VT_THREADS) bcg_update_p(const Chunk* __restrict__ chunks, const BatchMat* mats,
                                                            const int32_t* sys_off, const SysState* st,
                                                            const double* __restrict__ R, double* __restrict__ P,
-                                                           float* __restrict__ P32) {
+                                                           float* __restrict__ P32, double* __restrict__ X) {
     const Chunk ch = chunks[blockIdx.x];
     const int k = mats[ch.mat].k;
     const int64_t e0 = ch.off, e1 = ch.off + (int64_t)(ch.row1 - ch.row0) * k;
-    const double beta = st[sys_of(sys_off, ch.mat, threadIdx.x % k)].beta;
+    const SysState& y = st[sys_of(sys_off, ch.mat, threadIdx.x % k)];
+    const double beta = y.beta, alpha = y.alpha;
     for (int64_t e = e0 + threadIdx.x; e < e1; e += CHUNK_ILP * VT_THREADS) {
-        double r[CHUNK_ILP], p[CHUNK_ILP];
+        double r[CHUNK_ILP], p[CHUNK_ILP], x[CHUNK_ILP];
 #pragma unroll
         for (int u = 0; u < CHUNK_ILP; ++u) {
             const int64_t i = e + u * VT_THREADS;
             if (i < e1) {
                 r[u] = R[i];
                 p[u] = P[i];
+                if (X) x[u] = X[i];
             }
         }
 #pragma unroll
         for (int u = 0; u < CHUNK_ILP; ++u) {
             const int64_t i = e + u * VT_THREADS;
             if (i < e1) {
+                if (X) X[i] = x[u] + alpha * p[u];
                 const double pn = r[u] + beta * p[u];
                 P[i] = pn;
                 if (P32) P32[i] = csrk::dev::f64_to_f32(pn);
@@ -1095,10 +1103,11 @@ int bcg_enqueue_iteration(csrk_batch* b, cudaStream_t s) {
     if ((rc = launch_batch_spmm(b, b->d_mats_pq, 1.0, 0.0, s))) return rc;   // Q = A P
     bcg_dot<double><<<gv, VT_THREADS, 0, s>>>(b->d_chunks, b->d_mats_pq, b->P, b->Q, b->partials);
     bcg_fin(b, s, 1);
-    bcg_update_xr<double><<<gv, VT_THREADS, 0, s>>>(b->d_chunks, b->d_mats_pq, b->d_sys_off, b->st, b->X, b->R,
-                                                    b->P, b->Q, b->partials);
+    bcg_update_xr<double><<<gv, VT_THREADS, 0, s>>>(b->d_chunks, b->d_mats_pq, b->d_sys_off, b->st, nullptr,
+                                                    b->R, b->P, b->Q, b->partials);
     bcg_fin(b, s, 2);
-    bcg_update_p<<<gv, VT_THREADS, 0, s>>>(b->d_chunks, b->d_mats_pq, b->d_sys_off, b->st, b->R, b->P, nullptr);
+    bcg_update_p<<<gv, VT_THREADS, 0, s>>>(b->d_chunks, b->d_mats_pq, b->d_sys_off, b->st, b->R, b->P, nullptr,
+                                           b->X);
     CK_CUDA(cudaGetLastError(), "batched CG launch");
     return CSRK_OK;
 }
@@ -1115,18 +1124,18 @@ int bsolve_enqueue_cycle(csrk_batch* b, cudaStream_t s, bool mixed, int32_t E, i
             if ((rc = launch_batch_spmm(b, b->d_mats_lo, 1.0, 0.0, s))) return rc;   // Q32 = A_lo P32
             bcg_dot<float><<<gv, VT_THREADS, 0, s>>>(b->d_chunks, b->d_mats_pq, b->P, b->Q32, b->partials);
             bcg_fin(b, s, 1);
-            bcg_update_xr<float><<<gv, VT_THREADS, 0, s>>>(b->d_chunks, b->d_mats_pq, b->d_sys_off, b->st, b->X,
+            bcg_update_xr<float><<<gv, VT_THREADS, 0, s>>>(b->d_chunks, b->d_mats_pq, b->d_sys_off, b->st, nullptr,
                                                            b->R, b->P, b->Q32, b->partials);
         } else {
             if ((rc = launch_batch_spmm(b, b->d_mats_pq64, 1.0, 0.0, s))) return rc;   // Q = A64 P
             bcg_dot<double><<<gv, VT_THREADS, 0, s>>>(b->d_chunks, b->d_mats_pq, b->P, b->Q, b->partials);
             bcg_fin(b, s, 1);
-            bcg_update_xr<double><<<gv, VT_THREADS, 0, s>>>(b->d_chunks, b->d_mats_pq, b->d_sys_off, b->st, b->X,
+            bcg_update_xr<double><<<gv, VT_THREADS, 0, s>>>(b->d_chunks, b->d_mats_pq, b->d_sys_off, b->st, nullptr,
                                                             b->R, b->P, b->Q, b->partials);
         }
         bcg_fin(b, s, 2, 0.0, nullptr, o2);
         bcg_update_p<<<gv, VT_THREADS, 0, s>>>(b->d_chunks, b->d_mats_pq, b->d_sys_off, b->st, b->R, b->P,
-                                               mixed ? b->P32 : nullptr);
+                                               mixed ? b->P32 : nullptr, b->X);
     }
     CK_CUDA(cudaMemcpyAsync(b->Q, b->B, (size_t)b->total * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy B");
     if ((rc = launch_batch_spmm(b, b->d_mats_t64, -1.0, 1.0, s))) return rc;   // Q = B - A64 X
