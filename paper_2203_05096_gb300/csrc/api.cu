@@ -342,24 +342,26 @@ int smem_budget(const csrk_matrix* h, int ctas) {
 }  // namespace csrk
 
 bool csrk::plan_stages(const TileStats& st, int val_bytes, int max_smem, int want_stages, int col_bytes,
-                       StagePlan& plan, int64_t x_bytes) {
+                       StagePlan& plan, int64_t x_bytes, bool with_ord) {
     auto r16 = [](int64_t v) { return (v + 15) & ~int64_t(15); };
+    // each slice is rounded out to 16-byte boundaries at both ends: room for the largest
+    // slice plus up to 16 bytes' worth of elements
     const int64_t srp = r16((int64_t)(st.max_srs + 8) * 4);
     const int64_t rp = r16((int64_t)(st.max_rows + 8) * 4);
-    const int64_t col = r16((st.max_nnz + 32 / col_bytes) * col_bytes);   // slice rounded out to 16 B
-    const int64_t val = r16((st.max_nnz + 16) * val_bytes);
+    const int64_t col = r16((st.max_nnz + 32 / col_bytes) * col_bytes);
+    const int64_t val = r16((st.max_nnz + 32 / val_bytes) * val_bytes);
     const int64_t xw = r16(x_bytes);
     // kernel 5 also stages the SSR's slice of the permutation (the fused unpermute)
     const int64_t pm = x_bytes > 0 ? rp : 0;
     // ... and, for irregular rows, the SSR's slice of the rows' length order
-    const int64_t od = x_bytes > 0 ? r16((int64_t)(st.max_rows + 16) * 2) : 0;
+    const int64_t od = x_bytes > 0 && with_ord ? r16((int64_t)(st.max_rows + 16) * 2) : 0;
     int64_t stage = srp + rp + col + val + xw + pm + od;
     stage = (stage + 127) & ~int64_t(127);
-    const int64_t header = 768;   // 16 stages x (2 mbarriers + one 32-byte descriptor)
-    int64_t fit = (max_smem - header) / stage;
-    int64_t s = std::min<int64_t>(fit, 16);
+    // header: per stage two mbarriers and one 32-byte descriptor
+    int64_t s = std::min<int64_t>(max_smem / (stage + 48), 16);
     if (want_stages > 0) s = std::min<int64_t>(s, want_stages);
-    if (s < 2 || stage > (int64_t)UINT32_MAX) return false;
+    const int64_t header = r16(48 * std::max<int64_t>(s, 1));
+    if (s < 2 || s * stage + header > max_smem || stage > (int64_t)UINT32_MAX) return false;
     plan.off_srp = 0;
     plan.off_rp = (uint32_t)srp;
     plan.off_col = (uint32_t)(srp + rp);
@@ -472,9 +474,10 @@ int resolve_config(csrk_matrix* h, int vt, KernelConfig& cfg, StagePlan& plan, i
         cfg.unroll = 8;
     if (cfg.kernel == 5 || cfg.kernel == 6) {   // the windows must fit the stages as well
         const int64_t xb = (int64_t)h->max_win * xsz;
+        const bool ord = h->d_rord != nullptr;
         if (cfg.ctas == 0)
-            cfg.ctas = plan_stages(h->stats, (int)val_size(vt), smem_budget(h, 2), cfg.stages, 2, plan, xb) ? 2 : 1;
-        if (plan_stages(h->stats, (int)val_size(vt), smem_budget(h, cfg.ctas), cfg.stages, 2, plan, xb))
+            cfg.ctas = plan_stages(h->stats, (int)val_size(vt), smem_budget(h, 2), cfg.stages, 2, plan, xb, ord) ? 2 : 1;
+        if (plan_stages(h->stats, (int)val_size(vt), smem_budget(h, cfg.ctas), cfg.stages, 2, plan, xb, ord))
             return CSRK_OK;
         if (forced)
             return fail(CSRK_ERR_UNSUPPORTED, "super-super-rows and their x windows too large for two "
@@ -946,9 +949,10 @@ int autotune(csrk_matrix* h) {
     for (size_t b = 0; b < std::min<size_t>(3, phase1.size()) && rc == CSRK_OK; ++b) {
         if ((rc = install(phase1[b].sr, phase1[b].ssr)) || (rc = ensure_struct(h))) break;
         for (auto& pr : pairs)
-            for (int warps : {8, 16})
+            for (int warps : {4, 6, 8, 16})
                 for (int kernel : {0, 1, 2, 3, 4, 5, 6})
                     for (int ctas : {1, 2, 3, 4}) {
+                        if (warps < 8 && (kernel != 5 || ctas < 3)) continue;   // small blocks in numbers
                         if ((kernel == 1 || kernel == 3) && ctas >= 2) continue;
                         if (ctas >= 3 && (kernel < 4 || warps > 8)) continue;   // fits only small blocks
                         if (ctas == 4 && kernel != 5) continue;

@@ -159,10 +159,10 @@ struct StagePlan {
     uint32_t off_srp, off_rp, off_col, off_val, off_x, off_perm, off_ord, stage_bytes, header_bytes;
     int stages;
 };
-// x_bytes: room for the x window per stage (kernel 5, which also stages the SSR's slice of
-// the permutation; 0 otherwise).
+// x_bytes: room for the x window per stage (kernels 5 / 6, which also stage the SSR's slice
+// of the permutation, and with with_ord its rows' length order; 0 otherwise).
 bool plan_stages(const TileStats& st, int val_bytes, int max_smem, int want_stages, int col_bytes,
-                 StagePlan& plan, int64_t x_bytes = 0);
+                 StagePlan& plan, int64_t x_bytes = 0, bool with_ord = false);
 
 // spmv_*.cu: launch on `stream`; returns a cudaError_t value (0 = success) or -1 when the
 // combination is not compiled in.
