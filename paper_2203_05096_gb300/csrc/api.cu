@@ -351,8 +351,8 @@ bool csrk::plan_stages(const TileStats& st, int val_bytes, int max_smem, int wan
     const int64_t col = r16((st.max_nnz + 32 / col_bytes) * col_bytes);
     const int64_t val = r16((st.max_nnz + 32 / val_bytes) * val_bytes);
     const int64_t xw = r16(x_bytes);
-    // kernel 5 also stages the SSR's slice of the permutation (the fused unpermute)
-    const int64_t pm = x_bytes > 0 ? rp : 0;
+    // kernels 4 to 6 also stage the SSR's slice of the permutation (the fused unpermute)
+    const int64_t pm = x_bytes > 0 || col_bytes == 2 ? rp : 0;
     // ... and, for irregular rows, the SSR's slice of the rows' length order
     const int64_t od = x_bytes > 0 && with_ord ? r16((int64_t)(st.max_rows + 16) * 2) : 0;
     int64_t stage = srp + rp + col + val + xw + pm + od;

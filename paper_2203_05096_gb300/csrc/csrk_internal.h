@@ -159,8 +159,9 @@ struct StagePlan {
     uint32_t off_srp, off_rp, off_col, off_val, off_x, off_perm, off_ord, stage_bytes, header_bytes;
     int stages;
 };
-// x_bytes: room for the x window per stage (kernels 5 / 6, which also stage the SSR's slice
-// of the permutation, and with with_ord its rows' length order; 0 otherwise).
+// x_bytes: room for the x window per stage (kernels 5 / 6; 0 otherwise), with_ord: room for
+// the SSR's slice of the rows' length order (kernels 5 / 6).  The 16-bit-column kernels
+// (col_bytes 2: kernels 4 to 6) also stage the SSR's slice of the permutation.
 bool plan_stages(const TileStats& st, int val_bytes, int max_smem, int want_stages, int col_bytes,
                  StagePlan& plan, int64_t x_bytes = 0, bool with_ord = false);
 

@@ -251,8 +251,8 @@ __device__ __forceinline__ void store_y(XT* y, int64_t idx, AT acc, double alpha
 // every further entry the step from the previous column, so the lane rebuilds the column
 // with one integer add per nonzero.
 // LOCAL (kernel 5): CT = uint16_t codes are offsets into the SSR's x window, which x
-// points to in shared memory (one row per lane); yperm, when set, is the SSR's staged
-// slice of the permutation, also in shared memory.
+// points to in shared memory (one row per lane).  With 16-bit codes (kernels 4 and 5)
+// yperm, when set, is the SSR's staged slice of the permutation, in shared memory.
 template <typename VT, typename XT, typename AT, int LPR, int U, typename CT = int32_t, bool LOCAL = false>
 __device__ __forceinline__ void spmv_rows(int rb, int re, const int32_t* __restrict__ rp,
                                           const CT* __restrict__ col_s,
@@ -360,7 +360,7 @@ __device__ __forceinline__ void spmv_rows(int rb, int re, const int32_t* __restr
             for (int off = LPR / 2; off > 0; off >>= 1)
                 acc += __shfl_xor_sync(0xffffffffu, acc, off);
         }
-        if constexpr (LOCAL) {   // the permutation slice is staged in shared memory
+        if constexpr (sizeof(CT) == 2) {   // kernels 4, 5: the permutation slice is staged in shared memory
             if (base + lane < re) store_y<XT, AT>(y, yperm ? yperm[r] : r, acc, alpha, beta, epi);
         } else {
             if (r < re && sub == 0) store_y<XT, AT>(y, yperm ? __ldg(&yperm[r]) : r, acc, alpha, beta, epi);
@@ -827,7 +827,11 @@ __global__ void __launch_bounds__(544, 2) csr3_tma_kernel(const TmaParams P) {
                 slice16<4>(d.r0, (int64_t)d.r1 + 1, o_rp, b_rp);
                 slice16<CSZ>(d.p0, d.p1, o_col, b_col);
                 slice16<sizeof(VT)>(d.p0, d.p1, o_val, b_val);
-                mbar_arrive_expect_tx(&full[s], b_srp + b_rp + b_col + b_val);
+                uint32_t b_pm = 0;
+                int64_t o_pm = 0;
+                if (MODE == 3 && P.yperm) slice16<4>(d.r0, d.r1, o_pm, b_pm);   // the fused unpermute's targets
+                mbar_arrive_expect_tx(&full[s], b_srp + b_rp + b_col + b_val + b_pm);
+                if (b_pm) bulk_g2s(st + P.off_perm, P.yperm + o_pm, b_pm, &full[s], pol);
                 bulk_g2s(st + P.off_srp, P.sr_ptr + o_srp, b_srp, &full[s], pol);
                 bulk_g2s(st + P.off_rp, P.rowptr + o_rp, b_rp, &full[s], pol);
                 if (b_col)
@@ -873,7 +877,7 @@ __global__ void __launch_bounds__(544, 2) csr3_tma_kernel(const TmaParams P) {
             const int rb = srp[sr], re = srp[sr + 1];
 #ifdef CSRK_CHECKS
             {
-                const int32_t* yp = (MODE == 4 || MODE == 5) && P.yperm
+                const int32_t* yp = (MODE == 3 || MODE == 4 || MODE == 5) && P.yperm
                                         ? reinterpret_cast<const int32_t*>(st + P.off_perm) - (d.r0 & ~3)
                                         : P.yperm;
                 bool ok;
@@ -897,8 +901,9 @@ __global__ void __launch_bounds__(544, 2) csr3_tma_kernel(const TmaParams P) {
                 spmv_rows<VT, XT, AT, LPR, U>(rb, re, rp, col, val, x, y, P.alpha, P.beta, P.epi,
                                               lane, P.yperm);
             else if constexpr (MODE == 3)
-                spmv_rows<VT, XT, AT, LPR, U, uint16_t>(rb, re, rp, col16, val, x + d.cbase, y, P.alpha,
-                                                        P.beta, P.epi, lane, P.yperm);
+                spmv_rows<VT, XT, AT, LPR, U, uint16_t>(
+                    rb, re, rp, col16, val, x + d.cbase, y, P.alpha, P.beta, P.epi, lane,
+                    P.yperm ? reinterpret_cast<const int32_t*>(st + P.off_perm) - (d.r0 & ~3) : nullptr);
             else if constexpr (MODE == 5)
                 spmv_rows_ds_win<U>(rb, re, rp, col16, val, st + P.off_x, slow, y, P.alpha, P.beta, P.epi, lane,
                                     P.yperm ? reinterpret_cast<const int32_t*>(st + P.off_perm) - (d.r0 & ~3)

@@ -427,7 +427,8 @@ def test_autotuner_picks_a_working_config():
     inf = csrk.info(h)
     cfg = csrk.tuned_config(h)
     assert inf["sr"] > 0 and inf["ssr"] > 0 and inf["nssr"] > 0
-    assert cfg["kernel"] in (0, 1) and cfg["warps"] in (8, 16)
+    # on a matrix this small every shape is launch-bound: any timed candidate may win
+    assert 0 <= cfg["kernel"] <= 6 and cfg["warps"] in (4, 6, 8, 16) and 1 <= cfg["ctas"] <= 4
     assert_close(gpu_spmv(h, x), a, a.vals, x)
     # a second handle with the same shape reuses the cached choice
     h2 = csrk.create(a.n, a.rowptr, a.colidx, a.vals)
