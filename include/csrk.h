@@ -407,6 +407,28 @@ int csrk_model_sizes(double rdensity, int arch, int32_t* ssrs, int32_t* srs);
 int csrk_xwin_info(csrk_handle h, int32_t* available, int64_t* runs, int32_t* max_window,
                    int32_t* row_order);
 
+/* csrk_xwin_export: the x windows and the rows' length order that csrk_xwin_info
+ * describes, built on the host for the current pointers (no device needed, nothing
+ * uploaded; for tests and inspection).  Outputs (any may be NULL):
+ *   *available  1 when every super-super-row's window fits the 16-bit offsets, else 0
+ *               (then only ord and slots are written)
+ *   *nruns      runs over all super-super-rows
+ *   wptr        nssr + 1 entries: SSR t's runs are entries wptr[t] .. wptr[t+1]-1 of win
+ *   win         2 * nruns entries: per run its first element of x (a multiple of 4, in the
+ *               reordered numbering) and its offset in the window (runs of 4-element blocks
+ *               of the SSR's columns; runs at most 2 blocks apart are merged)
+ *   cover       nssr entries: elements of x the SSR's runs cover (its last run may end at n)
+ *   codes       nnz entries: per stored entry (reordered matrix, csrk_export's order) the
+ *               window offset of its column; entries of split long rows are 0
+ *   ord         one entry per row the super-rows cover: position i of an SSR starting at
+ *               row r0 holds row r0 + ord[i] (rows by decreasing length, ties in row order)
+ *   slots       2 entries: FP64 issue slots of all warp passes (per pass: its longest row)
+ *               in the natural and in the length order; the kernels use the order when it
+ *               saves at least 5 %
+ * Errors: CSRK_ERR_ARG, CSRK_ERR_STATE (no pointers yet), CSRK_ERR_ALLOC. */
+int csrk_xwin_export(csrk_handle h, int32_t* available, int64_t* nruns, int32_t* wptr, int32_t* win,
+                     int32_t* cover, uint16_t* codes, uint16_t* ord, int64_t* slots);
+
 /* csrk_tuned_config: the launch configuration the handle will use (any pointer may be
  * NULL):
  *   kernel   0 = TMA-staged super-super-row kernel, 1 = direct-load kernel, 2 / 3 = the

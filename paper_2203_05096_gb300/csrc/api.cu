@@ -1323,6 +1323,42 @@ int csrk_export(csrk_handle h, int32_t* perm, int32_t* rowptr, int32_t* colidx, 
     return CSRK_OK;
 }
 
+int csrk_xwin_export(csrk_handle h, int32_t* available, int64_t* nruns, int32_t* wptr, int32_t* win,
+                     int32_t* cover, uint16_t* codes, uint16_t* ord, int64_t* slots) {
+    if (!h) return fail(CSRK_ERR_ARG, "handle is NULL");
+    if (!h->have_ptrs) return fail(CSRK_ERR_STATE, "call csrk_set_sizes or csrk_set_pointers first");
+    try {
+        std::vector<SsrDesc> xdesc;
+        std::vector<int32_t> w, wp;
+        std::vector<uint16_t> colx;
+        int32_t mw = 0;
+        int64_t runs = 0;
+        const bool ok = !h->desc.empty() && build_xwin(h->m, h->desc, xdesc, w, wp, colx, mw, runs);
+        if (available) *available = ok ? 1 : 0;
+        if (nruns) *nruns = ok ? runs : 0;
+        if (ok) {
+            if (wptr) std::memcpy(wptr, wp.data(), sizeof(int32_t) * wp.size());
+            if (win && runs) std::memcpy(win, w.data(), sizeof(int32_t) * 2 * (size_t)runs);
+            if (cover)
+                for (size_t t = 0; t < xdesc.size(); ++t) cover[t] = xdesc[t].cbase;
+            if (codes && !colx.empty()) std::memcpy(codes, colx.data(), sizeof(uint16_t) * colx.size());
+        }
+        if (ord || slots) {
+            std::vector<uint16_t> o;
+            int64_t nat = 0, srt = 0;
+            build_row_order(h->m, h->sr_ptr, h->desc, o, nat, srt);
+            if (ord && !o.empty()) std::memcpy(ord, o.data(), sizeof(uint16_t) * o.size());
+            if (slots) {
+                slots[0] = nat;
+                slots[1] = srt;
+            }
+        }
+    } catch (const std::bad_alloc&) {
+        return fail(CSRK_ERR_ALLOC, "out of host memory");
+    }
+    return CSRK_OK;
+}
+
 int csrk_export_values(csrk_handle h, csrk_dtype dtype, void* out) {
     if (!h || !out) return fail(CSRK_ERR_ARG, "NULL argument");
     const int64_t nnz = h->m.nnz();

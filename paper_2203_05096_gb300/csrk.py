@@ -72,6 +72,7 @@ _PROTOS = {
     "csrk_batch_destroy": [_vp],
     "csrk_spmv_static_scratch": [_i32, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _d, _vp, _d, _vp, _vp],
     "csrk_xwin_info": [_vp, _vp, _vp, _vp, _vp],
+    "csrk_xwin_export": [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
 }
 
 
@@ -257,6 +258,27 @@ def xwin_info(h):
     _check(lib().csrk_xwin_info(h, ctypes.byref(av), ctypes.byref(runs), ctypes.byref(mw), ctypes.byref(ro)),
            "csrk_xwin_info")
     return dict(available=bool(av.value), runs=runs.value, max_window=mw.value, row_order=bool(ro.value))
+
+
+def xwin_export(h):
+    """The x windows and rows' length order, built on the host (csrk_xwin_export): dict(available,
+    wptr, win (runs x 2), cover, codes, ord, slots=(natural, ordered))."""
+    d = info(h)
+    av, nr = ctypes.c_int32(), ctypes.c_int64()
+    p = lambda a: a.ctypes.data_as(_vp)
+    _check(lib().csrk_xwin_export(h, ctypes.byref(av), ctypes.byref(nr), None, None, None, None, None, None),
+           "csrk_xwin_export")
+    wptr = np.zeros(d["nssr"] + 1, np.int32)
+    win = np.zeros((max(nr.value, 0), 2), np.int32)
+    cover = np.zeros(d["nssr"], np.int32)
+    codes = np.zeros(d["nnz"], np.uint16)
+    covered = int(export(h)["sr_ptr"][-1]) if d["nsr"] else 0
+    ord_ = np.zeros(covered, np.uint16)
+    slots = np.zeros(2, np.int64)
+    _check(lib().csrk_xwin_export(h, ctypes.byref(av), ctypes.byref(nr), p(wptr), p(win), p(cover), p(codes),
+                                  p(ord_), p(slots)), "csrk_xwin_export")
+    return dict(available=bool(av.value), wptr=wptr, win=win, cover=cover, codes=codes, ord=ord_,
+                slots=(int(slots[0]), int(slots[1])))
 
 
 def set_config(h, kernel=-1, lanes=-1, unroll=-1, warps=-1, stages=-1, ctas=-1):
