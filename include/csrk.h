@@ -176,6 +176,16 @@ int csrk_set_sizes(csrk_handle h, int32_t sr, int32_t ssr);
  * instead of 4; else 32.  Needs the pointer arrays (CSRK_ERR_STATE before).  Host only. */
 int csrk_index_bits(csrk_handle h, int32_t* bits);
 
+/* csrk_col16_export: kernel 4's delta-coded columns for the current pointers, built on the
+ * host (no device needed, nothing uploaded; for tests and inspection).
+ *   codes  nnz entries (reordered matrix, csrk_export's order): a row's first entry holds
+ *          its column minus its super-super-row's cbase, every further entry the step
+ *          from the previous column; entries of split long rows are 0
+ *   cbase  nssr entries: the smallest column of each super-super-row
+ * Either may be NULL.  Errors: CSRK_ERR_ARG, CSRK_ERR_STATE (no pointers yet),
+ * CSRK_ERR_UNSUPPORTED (csrk_index_bits would report 32), CSRK_ERR_ALLOC. */
+int csrk_col16_export(csrk_handle h, uint16_t* codes, int32_t* cbase);
+
 /* csrk_set_pointers: give the super-row and super-super-row pointer arrays explicitly
  * (variable sizes, e.g. Fig. 1: sr_ptr = {0,2,5,7,9}, ssr_ptr = {0,2,4}).
  *   nsr     number of super-rows; sr_ptr has nsr+1 entries, sr_ptr[0] = 0,

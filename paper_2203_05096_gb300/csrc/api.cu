@@ -1210,6 +1210,22 @@ int csrk_index_bits(csrk_handle h, int32_t* bits) {
     return CSRK_OK;
 }
 
+int csrk_col16_export(csrk_handle h, uint16_t* codes, int32_t* cbase) {
+    if (!h) return fail(CSRK_ERR_ARG, "handle is NULL");
+    if (!h->have_ptrs) return fail(CSRK_ERR_STATE, "call csrk_set_sizes or csrk_set_pointers first");
+    try {
+        std::vector<uint16_t> tmp;
+        if (!compress_columns(h->m, h->desc, tmp))
+            return fail(CSRK_ERR_UNSUPPORTED, "a column step or first-column offset exceeds 65,535");
+        if (codes && !tmp.empty()) std::memcpy(codes, tmp.data(), sizeof(uint16_t) * tmp.size());
+        if (cbase)
+            for (size_t t = 0; t < h->desc.size(); ++t) cbase[t] = h->desc[t].cbase;
+    } catch (const std::bad_alloc&) {
+        return fail(CSRK_ERR_ALLOC, "out of host memory");
+    }
+    return CSRK_OK;
+}
+
 int csrk_xwin_info(csrk_handle h, int32_t* available, int64_t* runs, int32_t* max_window,
                    int32_t* row_order) {
     if (!h) return fail(CSRK_ERR_ARG, "handle is NULL");

@@ -73,6 +73,7 @@ _PROTOS = {
     "csrk_spmv_static_scratch": [_i32, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _d, _vp, _d, _vp, _vp],
     "csrk_xwin_info": [_vp, _vp, _vp, _vp, _vp],
     "csrk_xwin_export": [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
+    "csrk_col16_export": [_vp, _vp, _vp],
 }
 
 
@@ -279,6 +280,15 @@ def xwin_export(h):
                                   p(ord_), p(slots)), "csrk_xwin_export")
     return dict(available=bool(av.value), wptr=wptr, win=win, cover=cover, codes=codes, ord=ord_,
                 slots=(int(slots[0]), int(slots[1])))
+
+
+def col16_export(h):
+    """Kernel 4's delta-coded columns built on the host (csrk_col16_export): dict(codes, cbase)."""
+    d = info(h)
+    codes = np.zeros(d["nnz"], np.uint16)
+    cbase = np.zeros(d["nssr"], np.int32)
+    _check(lib().csrk_col16_export(h, codes.ctypes.data_as(_vp), cbase.ctypes.data_as(_vp)), "csrk_col16_export")
+    return dict(codes=codes, cbase=cbase)
 
 
 def set_config(h, kernel=-1, lanes=-1, unroll=-1, warps=-1, stages=-1, ctas=-1):

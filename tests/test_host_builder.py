@@ -202,6 +202,67 @@ def test_index_bits_follow_the_ssr_column_span():
         csrk.destroy(h)
 
 
+def decode_col16(e, codes, cbase):
+    """Columns rebuilt from kernel 4's codes, row by row: the first code is an offset from the
+    row's super-super-row cbase, every further code the step from the previous column."""
+    out = np.zeros(len(codes), np.int64)
+    srp, ssrp, rp = e["sr_ptr"], e["ssr_ptr"], e["rowptr"]
+    for t in range(len(ssrp) - 1):
+        for r in range(int(srp[ssrp[t]]), int(srp[ssrp[t + 1]])):
+            p0, p1 = int(rp[r]), int(rp[r + 1])
+            if p1 > p0:
+                c = codes[p0:p1].astype(np.int64)
+                c[0] += int(cbase[t])
+                out[p0:p1] = np.cumsum(c)
+    return out
+
+
+@pytest.mark.parametrize("case", ["27pt_rcm", "fem_rcm", "random_empty_rows", "split_long_rows"])
+def test_col16_codes_decode_to_the_columns(case):
+    """Kernel 4's host coding (csrk_col16_export) rebuilt with the definition gives back every
+    column of every covered row; cbase is each SSR's smallest column; split long rows carry
+    no codes."""
+    split = 0
+    if case == "27pt_rcm":
+        a, sizes = synth.stencil_3d(14, 13, 12, 27, "random_dd", 8, labels=synth.vectors.permutation(2184, 8)), (32, 4)
+    elif case == "fem_rcm":
+        a, sizes = synth.fem_like(9, 4), (64, 2)
+    elif case == "random_empty_rows":
+        a, sizes = synth.random_pattern(3000, 0.002, 9, empty_rows=150, symmetric=True), (16, 8)
+    else:
+        a, sizes = synth.with_dense_rows(synth.stencil_3d(11, 10, 9, 7, "random_dd", 3), 2, 600, 4), (32, 2)
+        split = 400
+    h = csrk.create(a.n, a.rowptr, a.colidx, a.vals)
+    csrk.reorder(h)
+    if split:
+        csrk.split_long_rows(h, split)
+    csrk.set_sizes(h, *sizes)
+    e = csrk.export(h)
+    got = csrk.col16_export(h)
+    covered_nnz = int(e["rowptr"][e["sr_ptr"][-1]])
+    assert np.array_equal(decode_col16(e, got["codes"], got["cbase"])[:covered_nnz], e["colidx"][:covered_nnz])
+    assert not got["codes"][covered_nnz:].any()
+    rp, srp, ssrp = e["rowptr"], e["sr_ptr"], e["ssr_ptr"]
+    for t in range(len(ssrp) - 1):
+        p0, p1 = int(rp[srp[ssrp[t]]]), int(rp[srp[ssrp[t + 1]]])
+        assert got["cbase"][t] == (e["colidx"][p0:p1].min() if p1 > p0 else 0)
+    csrk.destroy(h)
+
+
+def test_col16_export_refused_when_the_coding_does_not_fit():
+    a = synth.stencil_3d(50, 50, 50, 7, "random_dd", 4, labels=synth.vectors.permutation(125000, 4))
+    h = csrk.create(a.n, a.rowptr, a.colidx, a.vals)
+    with pytest.raises(csrk.CsrkError) as ei:
+        csrk.col16_export(h)
+    assert ei.value.status == "ERR_STATE"
+    csrk.set_sizes(h, 32, 8)
+    assert csrk.index_bits(h) == 32
+    with pytest.raises(csrk.CsrkError) as ei:
+        csrk.col16_export(h)
+    assert ei.value.status == "ERR_UNSUPPORTED"
+    csrk.destroy(h)
+
+
 # ------------------------------------------------------------------ long rows
 def test_split_long_rows_moves_them_last():
     base = synth.stencil_3d(12, 12, 12, 7, "random_dd", 1, labels=synth.vectors.permutation(1728, 1))
