@@ -921,7 +921,7 @@ def run_reference(args, world, rank, local):
         flops += step()
     dt = time.perf_counter() - t0
     value = flops / dt / 1e9
-    sample = (f"every row of both 128^3 matrices per step (RCM by the oracle, {prep:.0f} s before timing), "
+    sample = (f"every row of both {args.side}^3 matrices per step (RCM by the oracle, {prep:.0f} s before timing), "
               f"Listing 1 loop nest, CSR-2 with 96-row super-rows, OpenMP static, {args.steps} steps in {dt:.2f} s")
     line = {
         "impl": "reference",
