@@ -552,6 +552,20 @@ int csrk_selftest_bounded_wait(csrk_handle h, uint64_t timeout_ns, void* stream,
  * for bit for every input but NaN (both NaN).  Errors: CSRK_ERR_ARG, CSRK_ERR_CUDA. */
 int csrk_selftest_narrow(const double* x, int64_t n, float* by_int, float* by_cvt, void* stream);
 
+/* csrk_selftest_stage_plan: the shared-memory stage layout the TMA kernels use for SSRs of
+ * at most max_srs super-rows, max_rows rows and max_nnz nonzeros, values of val_bytes and
+ * stored columns of col_bytes (2 = 16-bit codes), within max_smem bytes of shared memory
+ * per block, at most want_stages stages (0 = as many as fit, up to 16), x_bytes of x
+ * window per stage (kernels 5 / 6; 0 otherwise) and with_ord != 0 for the rows' length
+ * order.  Host only, for tests.  out[10] receives the byte offsets inside a stage of the
+ * sr_ptr, rowptr, column, value, x-window, permutation and length-order slices, the stage
+ * size, the header size (mbarriers and descriptors) and the stage count; the kernels copy
+ * each slice rounded out to 16-byte boundaries at both ends.  Errors: CSRK_ERR_ARG,
+ * CSRK_ERR_UNSUPPORTED when two stages do not fit. */
+int csrk_selftest_stage_plan(int32_t max_srs, int32_t max_rows, int64_t max_nnz, int32_t val_bytes,
+                             int32_t col_bytes, int32_t max_smem, int32_t want_stages, int64_t x_bytes,
+                             int32_t with_ord, uint32_t* out);
+
 const char* csrk_last_error(void);
 
 /* Library build description (static string): compiled architectures and options. */

@@ -1499,6 +1499,26 @@ int csrk_selftest_narrow(const double* x, int64_t n, float* by_int, float* by_cv
     return CSRK_OK;
 }
 
+int csrk_selftest_stage_plan(int32_t max_srs, int32_t max_rows, int64_t max_nnz, int32_t val_bytes,
+                             int32_t col_bytes, int32_t max_smem, int32_t want_stages, int64_t x_bytes,
+                             int32_t with_ord, uint32_t* out) {
+    if (!out || max_srs < 0 || max_rows < 0 || max_nnz < 0 || x_bytes < 0 || max_smem <= 0 ||
+        (val_bytes != 2 && val_bytes != 4 && val_bytes != 8) || (col_bytes != 2 && col_bytes != 4))
+        return fail(CSRK_ERR_ARG, "bad arguments");
+    TileStats st;
+    st.max_srs = max_srs;
+    st.max_rows = max_rows;
+    st.max_nnz = max_nnz;
+    StagePlan plan{};
+    if (!plan_stages(st, val_bytes, max_smem, want_stages, col_bytes, plan, x_bytes, with_ord != 0))
+        return fail(CSRK_ERR_UNSUPPORTED, "no two stages fit");
+    const uint32_t v[10] = {plan.off_srp, plan.off_rp, plan.off_col, plan.off_val, plan.off_x,
+                            plan.off_perm, plan.off_ord, plan.stage_bytes, plan.header_bytes,
+                            (uint32_t)plan.stages};
+    std::memcpy(out, v, sizeof v);
+    return CSRK_OK;
+}
+
 const char* csrk_last_error(void) { return g_last_error.c_str(); }
 
 const char* csrk_build_info(void) {

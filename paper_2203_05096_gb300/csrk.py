@@ -74,6 +74,7 @@ _PROTOS = {
     "csrk_xwin_info": [_vp, _vp, _vp, _vp, _vp],
     "csrk_xwin_export": [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "csrk_col16_export": [_vp, _vp, _vp],
+    "csrk_selftest_stage_plan": [_i32, _i32, _i64, _i32, _i32, _i32, _i32, _i64, _i32, _vp],
 }
 
 
@@ -289,6 +290,18 @@ def col16_export(h):
     cbase = np.zeros(d["nssr"], np.int32)
     _check(lib().csrk_col16_export(h, codes.ctypes.data_as(_vp), cbase.ctypes.data_as(_vp)), "csrk_col16_export")
     return dict(codes=codes, cbase=cbase)
+
+
+def stage_plan(max_srs, max_rows, max_nnz, val_bytes, col_bytes, max_smem, want_stages=0, x_bytes=0,
+               with_ord=False):
+    """The TMA kernels' shared-memory stage layout (csrk_selftest_stage_plan) as a dict."""
+    out = np.zeros(10, np.uint32)
+    _check(lib().csrk_selftest_stage_plan(int(max_srs), int(max_rows), int(max_nnz), int(val_bytes),
+                                          int(col_bytes), int(max_smem), int(want_stages), int(x_bytes),
+                                          int(bool(with_ord)), out.ctypes.data_as(_vp)), "csrk_selftest_stage_plan")
+    keys = ("off_srp", "off_rp", "off_col", "off_val", "off_x", "off_perm", "off_ord", "stage_bytes",
+            "header_bytes", "stages")
+    return dict(zip(keys, (int(v) for v in out)))
 
 
 def set_config(h, kernel=-1, lanes=-1, unroll=-1, warps=-1, stages=-1, ctas=-1):
